@@ -1,0 +1,896 @@
+// Host side of the C ABI declared in include/lbm.h.
+//
+// A simulation owns its device buffers and four CUDA graphs: one time step
+// and two time steps, each for either population buffer as the source.  A
+// time step is the chain moments -> force -> u-solve -> derivatives ->
+// collide; the u-solve is a WHILE conditional node whose body is one Jacobi
+// sweep (q, j~new) followed by a one-thread control kernel that tests
+// convergence on the device and sets the loop condition, so a step never
+// returns to the host.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_common.h"
+#include "lbm_lattice.h"
+
+using namespace lbm;
+
+namespace {
+
+constexpr int MAX_AUX = 26;
+
+struct Graphs {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+};
+
+}  // namespace
+
+struct lbm_sim {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int lattice = 0, d = 0, Q = 0;
+    int64_t dims[3] = {0, 0, 0};
+    lbm_eos eos{};
+    lbm_params prm{};
+    KernelTable kt{};
+    DevSim dev{};
+    int cur = 0;  // population buffer holding the current pre-collision populations
+    int64_t steps = 0;
+    std::vector<void*> allocs;
+    double* red_part = nullptr;
+    double* red_out = nullptr;
+    Graphs one[2], two[2];
+};
+
+namespace {
+
+#define LBM_CK(call)                                                  \
+    do {                                                              \
+        cudaError_t e_ = (call);                                      \
+        if (e_ != cudaSuccess) {                                      \
+            (void)cudaGetLastError();                                 \
+            return e_ == cudaErrorMemoryAllocation ? LBM_E_OOM : LBM_E_CUDA; \
+        }                                                             \
+    } while (0)
+
+int nblocks(long long N, int block) { return int((N + block - 1) / block); }
+
+// grid of the tiled kernels: one CTA per TX x TY column tile and z-slab
+dim3 tile_grid(const lbm_sim* s);
+
+void host_eos(const lbm_eos& e, double rho, double out[4])
+{
+    double p, dp, d2p;
+    if (e.kind == LBM_EOS_VDW) {
+        const double g = 1.0 - e.b * rho;
+        p = rho * e.T / g - e.a * rho * rho;
+        dp = e.T / (g * g) - 2.0 * e.a * rho;
+        d2p = 2.0 * e.b * e.T / (g * g * g) - 2.0 * e.a;
+    } else {
+        const double D = e.rho2 - e.rho1, rho3 = 2.0 * e.rho2 - e.rho1;
+        double psi = 0.0, dpsi = 0.0, integ = 0.0;
+        if (rho > e.rho1 && rho < rho3) {
+            const double ph = M_PI * (rho - e.rho1) / D;
+            psi = e.A * std::sin(ph);
+            dpsi = e.A * M_PI / D * std::cos(ph);
+            integ = e.A * D / M_PI * (1.0 - std::cos(ph));
+        }
+        const double cs2 = e.cs2_rho1 * std::exp(integ);
+        p = rho * cs2;
+        dp = cs2 * (1.0 + rho * psi);
+        d2p = cs2 * psi * (1.0 + rho * psi) + cs2 * (psi + rho * dpsi);
+    }
+    out[0] = p;
+    out[1] = dp;
+    out[2] = p - rho * dp;
+    out[3] = rho * d2p;
+}
+
+template <int LAT>
+double host_weight(int k, double s)
+{
+    using L = Lat<LAT>;
+    return L::wc(k, 0) + s * (L::wc(k, 1) + s * (L::wc(k, 2) + s * L::wc(k, 3)));
+}
+
+template <int LAT>
+double min_weight(double s)
+{
+    double m = 1e300;
+    for (int k = 0; k < Lat<LAT>::NSHELL; ++k) m = std::fmin(m, host_weight<LAT>(k, s));
+    return m;
+}
+
+// edges of the interval around s_in where every shell weight is positive
+template <int LAT>
+void weight_window(double& lo, double& hi)
+{
+    const double s_in = 0.6;  // inside the window of both lattices
+    double a = 0.01, b = s_in;
+    for (int it = 0; it < 200; ++it) {
+        const double m = 0.5 * (a + b);
+        (min_weight<LAT>(m) > 0.0 ? b : a) = m;
+    }
+    lo = b;
+    a = s_in;
+    b = 3.0;
+    for (int it = 0; it < 200; ++it) {
+        const double m = 0.5 * (a + b);
+        (min_weight<LAT>(m) > 0.0 ? a : b) = m;
+    }
+    hi = a;
+}
+
+// Largest eigenvalue of the u-solve iteration for frozen coefficients at density rho:
+// (|s|^2 / 12) max(3 c_s^2 - p', c_s^2), |s|^2 <= d max_k s(k)^2 with s(k) the symbol
+// (4/3) sin k - (1/6) sin 2k of the Sec. IV.B first derivative.
+double frozen_gain(const lbm_eos& e, double rho, int d)
+{
+    double smax = 0.0;
+    for (int k = 0; k <= 20000; ++k) {
+        const double x = M_PI * k / 20000.0;
+        smax = std::fmax(smax, std::fabs(4.0 / 3.0 * std::sin(x) - std::sin(2.0 * x) / 6.0));
+    }
+    double ev[4];
+    host_eos(e, rho, ev);
+    const double cs2 = ev[0] / rho;
+    return d * smax * smax / 12.0 * std::fmax(3.0 * cs2 - ev[1], cs2);
+}
+
+// omega = 2 / (2 - g) for the spectrum [0, g] of the iteration, g from the frozen
+// coefficients over the create-time density range (with 2 % margin); 1 without a range.
+double auto_omega(const lbm_eos& e, const lbm_params& prm, int d)
+{
+    if (!(prm.rho_check_max > prm.rho_check_min && prm.rho_check_min > 0.0)) return 1.0;
+    double g = 0.0;
+    for (int k = 0; k <= 400; ++k)
+        g = std::fmax(g, frozen_gain(e, prm.rho_check_min + (prm.rho_check_max - prm.rho_check_min) * k / 400.0, d));
+    g = std::fmin(0.95, 1.02 * g);
+    return 2.0 / (2.0 - g);
+}
+
+size_t bytes_per_site(int lattice, int storage, size_t* ssize_out = nullptr)
+{
+    const int Q = lattice == LBM_D3Q59 ? 59 : 21;
+    const int naux = lattice == LBM_D3Q59 ? 26 : 13;
+    size_t ssize = 4, tsize = 4;
+    if (storage == LBM_STORE_F16_DEV || storage == LBM_STORE_BF16_DEV) ssize = 2;
+    if (storage == LBM_STORE_F64) ssize = tsize = 8;
+    if (ssize_out) *ssize_out = ssize;
+    const size_t usize = 8;  // worst case: FP64 u-solve
+    const size_t rest = storage == LBM_STORE_F64 ? 0 : 2 * 8 + 4;  // two float-pair rest planes, rho_lo
+    return 2 * Q * ssize + rest + tsize * (1 + 3 + 3 + naux) + usize * (4 * 3 + 6);
+}
+
+int validate(int lattice, const int64_t dims[3], int storage)
+{
+    if (lattice != LBM_D2Q21 && lattice != LBM_D3Q59) return LBM_E_INVALID_ARG;
+    if (!dims) return LBM_E_INVALID_ARG;
+    if (storage < LBM_STORE_F32 || storage > LBM_STORE_F64) return LBM_E_INVALID_ARG;
+    if (dims[0] < 4 || dims[1] < 4) return LBM_E_INVALID_ARG;
+    if (lattice == LBM_D2Q21 && dims[2] != 1) return LBM_E_INVALID_ARG;
+    if (lattice == LBM_D3Q59 && dims[2] < 4) return LBM_E_INVALID_ARG;
+    if (dims[0] > (1 << 20) || dims[1] > (1 << 20) || dims[2] > (1 << 20)) return LBM_E_INVALID_ARG;
+    const double N = double(dims[0]) * double(dims[1]) * double(dims[2]);
+    const int Q = lattice == LBM_D3Q59 ? 59 : 21;
+    if (N * Q > 9.0e18 / 8.0) return LBM_E_INVALID_ARG;
+    return LBM_OK;
+}
+
+cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* out, const void* fn, dim3 grid, int block, void** args,
+                       const cudaGraphNode_t* deps, size_t ndeps, size_t smem = 0)
+{
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void*>(fn);
+    kp.gridDim = grid;
+    kp.blockDim = dim3(block);
+    kp.sharedMemBytes = (unsigned)smem;
+    kp.kernelParams = args;
+    kp.extra = nullptr;
+    return cudaGraphAddKernelNode(out, g, deps, ndeps, &kp);
+}
+
+// Append one time step (source buffer src) to graph g after dependency dep.
+int add_step(lbm_sim* s, cudaGraph_t g, cudaGraphNode_t dep, int src, cudaGraphNode_t* last)
+{
+    DevSim& dv = s->dev;
+    const int B = s->kt.block;
+    const int G = nblocks(dv.N, B);
+    int pair = 0, one = 1;
+    cudaGraphNode_t n1, n2, n3, nc, n5, n6;
+    const cudaGraphNode_t* d0 = dep ? &dep : nullptr;
+    size_t nd0 = dep ? 1 : 0;
+    {
+        void* a[] = {&dv, &src, &pair};
+        LBM_CK(add_kernel(g, &n1, s->kt.moments, dim3(G), B, a, d0, nd0));
+    }
+    {
+        void* a[] = {&dv};
+        LBM_CK(add_kernel(g, &n2, s->kt.force, dim3(G), B, a, &n1, 1));
+    }
+    {
+        void* a[] = {&dv, &pair};
+        LBM_CK(add_kernel(g, &n3, s->kt.us_begin, dim3(1), 1, a, &n2, 1));
+    }
+    cudaGraphConditionalHandle h;
+    LBM_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    LBM_CK(cudaGraphAddNode(&nc, g, &n3, nullptr, 1, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    const dim3 TG = tile_grid(s);
+    const int TB = s->kt.tile_threads;
+    {
+        cudaGraphNode_t b1, b3;
+        void* a1[] = {&dv, &pair};
+        LBM_CK(add_kernel(body, &b1, s->kt.sweep, TG, TB, a1, nullptr, 0, s->kt.smem_sweep));
+        void* a3[] = {&dv, &pair, &h, &one};
+        LBM_CK(add_kernel(body, &b3, s->kt.us_ctl, dim3(1), 1, a3, &b1, 1));
+    }
+    {
+        void* a[] = {&dv};
+        LBM_CK(add_kernel(g, &n5, s->kt.derivs, TG, TB, a, &nc, 1, s->kt.smem_derivs));
+    }
+    {
+        void* a[] = {&dv, &src};
+        LBM_CK(add_kernel(g, &n6, s->kt.collide, TG, TB, a, &n5, 1, s->kt.smem_collide));
+    }
+    *last = n6;
+    return LBM_OK;
+}
+
+int build_graphs(lbm_sim* s)
+{
+    for (int src = 0; src < 2; ++src) {
+        LBM_CK(cudaGraphCreate(&s->one[src].g, 0));
+        cudaGraphNode_t last;
+        int rc = add_step(s, s->one[src].g, nullptr, src, &last);
+        if (rc) return rc;
+        LBM_CK(cudaGraphInstantiate(&s->one[src].x, s->one[src].g, 0));
+        LBM_CK(cudaGraphCreate(&s->two[src].g, 0));
+        cudaGraphNode_t mid;
+        rc = add_step(s, s->two[src].g, nullptr, src, &mid);
+        if (rc) return rc;
+        rc = add_step(s, s->two[src].g, mid, src ^ 1, &last);
+        if (rc) return rc;
+        LBM_CK(cudaGraphInstantiate(&s->two[src].x, s->two[src].g, 0));
+    }
+    return LBM_OK;
+}
+
+int dev_alloc(lbm_sim* s, void** p, size_t bytes)
+{
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        *p = nullptr;
+        return e == cudaErrorMemoryAllocation ? LBM_E_OOM : LBM_E_CUDA;
+    }
+    s->allocs.push_back(*p);
+    return LBM_OK;
+}
+
+template <class... A>
+cudaError_t launch(const lbm_sim* s, const void* fn, int grid, int block, A... args)
+{
+    void* a[] = {&args...};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(block), a, 0, s->stream);
+}
+
+template <class... A>
+cudaError_t launch_tiled(const lbm_sim* s, const void* fn, size_t smem, A... args)
+{
+    void* a[] = {&args...};
+    return cudaLaunchKernel(fn, tile_grid(s), dim3(s->kt.tile_threads), a, smem, s->stream);
+}
+
+int read_status(lbm_sim* s, int* bits)
+{
+    int st = 0;
+    LBM_CK(cudaMemcpyAsync(&st, s->dev.status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    LBM_CK(cudaStreamSynchronize(s->stream));
+    if (st) {
+        const int z = 0;
+        LBM_CK(cudaMemcpyAsync(s->dev.status, &z, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+        LBM_CK(cudaStreamSynchronize(s->stream));
+    }
+    *bits = st;
+    return LBM_OK;
+}
+
+int status_code(int bits)
+{
+    if (bits & (STB_WEIGHTS | STB_NONFINITE_RHO)) return LBM_E_WEIGHTS;
+    if (bits & (STB_USOLVE_CAP | STB_USOLVE_NAN)) return LBM_E_USOLVE_DIVERGED;
+    return LBM_OK;
+}
+
+int reset_usolve(lbm_sim* s)
+{
+    UsolveState z[2];
+    std::memset(z, 0, sizeof(z));
+    LBM_CK(cudaMemcpyAsync(s->dev.us, z, sizeof(z), cudaMemcpyHostToDevice, s->stream));
+    const size_t jbytes = 3 * size_t(s->dev.N) * s->kt.usize;
+    for (int pr = 0; pr < 2; ++pr)
+        for (int b = 0; b < 2; ++b) LBM_CK(cudaMemsetAsync(s->dev.jt[pr][b], 0, jbytes, s->stream));
+    const int zi = 0;
+    LBM_CK(cudaMemcpyAsync(s->dev.status, &zi, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    return LBM_OK;
+}
+
+dim3 tile_grid(const lbm_sim* s)
+{
+    const int* t = s->kt.tile;
+    return dim3((s->dev.nx + t[0] - 1) / t[0], (s->dev.ny + t[1] - 1) / t[1],
+                s->d == 3 ? (s->dev.nz + t[2] - 1) / t[2] : 1);
+}
+
+// S1-S8 on the current populations with the scratch j~ pair; host-driven loop.
+int run_fields(lbm_sim* s)
+{
+    DevSim& dv = s->dev;
+    const int B = s->kt.block, G = nblocks(dv.N, B);
+    const int pair = 1;
+    LBM_CK(launch(s, s->kt.copy_jt, G, B, dv));
+    const int zero = 0;
+    LBM_CK(cudaMemcpyAsync(&dv.us[1].cur, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    LBM_CK(launch(s, s->kt.moments, G, B, dv, s->cur, pair));
+    LBM_CK(launch(s, s->kt.force, G, B, dv));
+    LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
+    cudaGraphConditionalHandle h{};
+    const int no = 0;
+    for (int it = 0; it < s->dev.maxit + 1; ++it) {
+        LBM_CK(launch_tiled(s, s->kt.sweep, s->kt.smem_sweep, dv, pair));
+        LBM_CK(launch(s, s->kt.us_ctl, 1, 1, dv, pair, h, no));
+        UsolveState u;
+        LBM_CK(cudaMemcpyAsync(&u, &dv.us[1], sizeof(u), cudaMemcpyDeviceToHost, s->stream));
+        LBM_CK(cudaStreamSynchronize(s->stream));
+        if (!u.running) break;  // the control kernel recorded a stop
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_error_string(int code)
+{
+    switch (code) {
+    case LBM_OK: return "ok";
+    case LBM_E_INVALID_ARG: return "invalid argument";
+    case LBM_E_WEIGHTS: return "c_s^2 left the positive-weight window or a density became non-finite";
+    case LBM_E_BULKVISC: return "equation of state not admissible (bulk viscosity or weights)";
+    case LBM_E_USOLVE_DIVERGED: return "u-solve did not converge within its sweep cap";
+    case LBM_E_OOM: return "out of device memory";
+    case LBM_E_CUDA: return "CUDA error or no usable device";
+    case LBM_E_TIMEOUT: return "device wait timed out";
+    case LBM_E_IO: return "checkpoint file error";
+    default: return "unknown error";
+    }
+}
+
+int lbm_velocities(int lattice, int* c_out)
+{
+    if (lattice == LBM_D2Q21) {
+        using L = Lat<0>;
+        if (c_out)
+            for (int i = 0; i < L::Q; ++i) { c_out[3 * i] = L::cx(i); c_out[3 * i + 1] = L::cy(i); c_out[3 * i + 2] = 0; }
+        return L::Q;
+    }
+    if (lattice == LBM_D3Q59) {
+        using L = Lat<1>;
+        if (c_out)
+            for (int i = 0; i < L::Q; ++i) { c_out[3 * i] = L::cx(i); c_out[3 * i + 1] = L::cy(i); c_out[3 * i + 2] = L::cz(i); }
+        return L::Q;
+    }
+    return LBM_E_INVALID_ARG;
+}
+
+size_t lbm_footprint_bytes(int lattice, const int64_t dims[3], int storage)
+{
+    if (validate(lattice, dims, storage) != LBM_OK) return 0;
+    const size_t N = size_t(dims[0]) * size_t(dims[1]) * size_t(dims[2]);
+    return N * bytes_per_site(lattice, storage) + 64 * 1024;
+}
+
+void lbm_destroy(lbm_sim* s)
+{
+    if (!s) return;
+    cudaSetDevice(s->device);
+    if (s->stream) cudaStreamSynchronize(s->stream);
+    for (int k = 0; k < 2; ++k) {
+        if (s->one[k].x) cudaGraphExecDestroy(s->one[k].x);
+        if (s->one[k].g) cudaGraphDestroy(s->one[k].g);
+        if (s->two[k].x) cudaGraphExecDestroy(s->two[k].x);
+        if (s->two[k].g) cudaGraphDestroy(s->two[k].g);
+    }
+    for (void* p : s->allocs) cudaFree(p);
+    (void)cudaGetLastError();
+    delete s;
+}
+
+int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm_params* params, void* cuda_stream,
+               lbm_sim** out)
+{
+    if (!out || !eos || !params) return LBM_E_INVALID_ARG;
+    *out = nullptr;
+    int rc = validate(lattice, dims, params->storage);
+    if (rc) return rc;
+    if (!(params->gamma > -1.0 && params->gamma < 1.0)) return LBM_E_INVALID_ARG;
+    if (!(params->kappa >= 0.0) || !(params->rho0 > 0.0)) return LBM_E_INVALID_ARG;
+    if (eos->kind != LBM_EOS_VDW && eos->kind != LBM_EOS_PSI_SINE) return LBM_E_INVALID_ARG;
+    if (eos->kind == LBM_EOS_PSI_SINE && !(eos->rho2 > eos->rho1 && eos->cs2_rho1 > 0.0)) return LBM_E_INVALID_ARG;
+    if (params->usolve_precision != LBM_USOLVE_NATIVE && params->usolve_precision != LBM_USOLVE_F64)
+        return LBM_E_INVALID_ARG;
+
+    const int d = lattice == LBM_D3Q59 ? 3 : 2;
+    double lo, hi;
+    if (lattice == LBM_D3Q59) weight_window<1>(lo, hi); else weight_window<0>(lo, hi);
+
+    // create-time admissibility of the EOS (App. B) over the density range of the run
+    double e0[4];
+    host_eos(*eos, params->rho0, e0);
+    const double cs0 = e0[0] / params->rho0;
+    if (!(cs0 > lo && cs0 < hi)) return LBM_E_WEIGHTS;
+    if (params->rho_check_max > params->rho_check_min && params->rho_check_min > 0.0) {
+        for (int k = 0; k <= 2000; ++k) {
+            const double r = params->rho_check_min + (params->rho_check_max - params->rho_check_min) * k / 2000.0;
+            double e[4];
+            host_eos(*eos, r, e);
+            const double cs2 = e[0] / r;
+            if (!(cs2 > lo && cs2 < hi)) return LBM_E_WEIGHTS;
+            if (!(r * e[1] / e[0] < 1.0 + 2.0 / d)) return LBM_E_BULKVISC;
+        }
+    }
+
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        (void)cudaGetLastError();
+        return LBM_E_CUDA;
+    }
+    lbm_sim* s = new (std::nothrow) lbm_sim();
+    if (!s) return LBM_E_OOM;
+    cudaGetDevice(&s->device);
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+    s->lattice = lattice;
+    s->d = d;
+    s->Q = lattice == LBM_D3Q59 ? 59 : 21;
+    for (int k = 0; k < 3; ++k) s->dims[k] = dims[k];
+    s->eos = *eos;
+    s->prm = *params;
+
+    const bool f64 = params->storage == LBM_STORE_F64;
+    const bool us64 = f64 || params->usolve_precision == LBM_USOLVE_F64;
+    const bool read_pops = params->gamma != 0.0;
+    bool ok = lattice == LBM_D3Q59 ? get_kernels_d3q59(params->storage, us64, read_pops, &s->kt)
+                                   : get_kernels_d2q21(params->storage, us64, read_pops, &s->kt);
+    if (!ok) { delete s; return LBM_E_INVALID_ARG; }
+
+    DevSim& dv = s->dev;
+    dv.lattice = lattice;
+    dv.d = d;
+    dv.Q = s->Q;
+    dv.nx = int(dims[0]);
+    dv.ny = int(dims[1]);
+    dv.nz = int(dims[2]);
+    dv.N = (long long)dims[0] * dims[1] * dims[2];
+    dv.gamma = params->gamma;
+    dv.kappa = params->kappa;
+    dv.rho0 = params->rho0;
+    dv.cs0 = cs0;
+    const int nshell = lattice == LBM_D3Q59 ? 8 : 6;
+    for (int k = 0; k < 8; ++k) {
+        dv.w0[k] = k < nshell ? (lattice == LBM_D3Q59 ? host_weight<1>(k, cs0) : host_weight<0>(k, cs0)) : 0.0;
+        dv.off[k] = dv.w0[k] * params->rho0;
+    }
+    dv.eos_kind = eos->kind;
+    dv.a = eos->a; dv.b = eos->b; dv.T = eos->T;
+    dv.rho1 = eos->rho1; dv.rho2 = eos->rho2; dv.A = eos->A; dv.cs2_1 = eos->cs2_rho1;
+    dv.cs2_lo = lo;
+    dv.cs2_hi = hi;
+    if (params->usolve_tol > 0.0 || params->usolve_rtol > 0.0) {
+        dv.tol = params->usolve_tol > 0.0 ? params->usolve_tol : 0.0;
+        dv.rtol = params->usolve_rtol > 0.0 ? params->usolve_rtol : 0.0;
+    } else if (us64) {
+        dv.tol = 1e-14;
+        dv.rtol = 0.0;
+    } else {
+        dv.tol = 5e-9;
+        dv.rtol = 0.0;
+    }
+    if (!(params->usolve_omega >= 0.0 && params->usolve_omega < 2.0)) { lbm_destroy(s); return LBM_E_INVALID_ARG; }
+    dv.omega = params->usolve_omega > 0.0 ? params->usolve_omega : auto_omega(*eos, *params, d);
+    dv.maxit = params->usolve_max_iter > 0 ? params->usolve_max_iter : 500;
+    dv.warm = params->usolve_warm_start ? 1 : 0;
+
+    const size_t N = size_t(dv.N);
+    const size_t T = s->kt.tsize, U = s->kt.usize, SS = s->kt.ssize;
+    rc = LBM_OK;
+    rc = rc ? rc : dev_alloc(s, &dv.pop[0], size_t(s->Q) * N * SS);
+    rc = rc ? rc : dev_alloc(s, &dv.pop[1], size_t(s->Q) * N * SS);
+    if (s->kt.rsize) {  // separate rest plane of the reduced storages
+        rc = rc ? rc : dev_alloc(s, &dv.pop0[0], N * s->kt.rsize);
+        rc = rc ? rc : dev_alloc(s, &dv.pop0[1], N * s->kt.rsize);
+    }
+    if (s->kt.exact) rc = rc ? rc : dev_alloc(s, &dv.rho_lo, N * sizeof(float));
+    rc = rc ? rc : dev_alloc(s, &dv.rho, N * T);
+    rc = rc ? rc : dev_alloc(s, &dv.j0p, 3 * N * T);
+    rc = rc ? rc : dev_alloc(s, &dv.f, 3 * N * T);
+    for (int pr = 0; pr < 2; ++pr)
+        for (int b = 0; b < 2; ++b) rc = rc ? rc : dev_alloc(s, &dv.jt[pr][b], 3 * N * U);
+    rc = rc ? rc : dev_alloc(s, &dv.q, 6 * N * U);
+    rc = rc ? rc : dev_alloc(s, &dv.aux, size_t(MAX_AUX) * N * T);
+    void* usp = nullptr;
+    rc = rc ? rc : dev_alloc(s, &usp, 2 * sizeof(UsolveState));
+    dv.us = static_cast<UsolveState*>(usp);
+    void* stp = nullptr;
+    rc = rc ? rc : dev_alloc(s, &stp, 256);
+    dv.status = static_cast<int*>(stp);
+    void* rp = nullptr;
+    rc = rc ? rc : dev_alloc(s, &rp, (kRedGrid * 4 + 8) * sizeof(double));
+    s->red_part = static_cast<double*>(rp);
+    s->red_out = s->red_part + kRedGrid * 4;
+    dv.red = s->red_part;
+    if (rc) { lbm_destroy(s); return rc; }
+    // well-defined contents before the first lbm_init
+    for (int b = 0; b < 2; ++b) {
+        if (cudaMemsetAsync(dv.pop[b], 0, size_t(s->Q) * N * SS, s->stream) != cudaSuccess ||
+            (dv.pop0[b] && cudaMemsetAsync(dv.pop0[b], 0, N * s->kt.rsize, s->stream) != cudaSuccess)) {
+            lbm_destroy(s);
+            return LBM_E_CUDA;
+        }
+    }
+    rc = reset_usolve(s);
+    if (!rc) rc = build_graphs(s);
+    if (!rc && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = LBM_E_CUDA;
+    if (rc) { lbm_destroy(s); return rc; }
+    *out = s;
+    return LBM_OK;
+}
+
+int lbm_init(lbm_sim* s, const double* rho, const double* u, int on_device)
+{
+    if (!s || !rho) return LBM_E_INVALID_ARG;
+    LBM_CK(cudaSetDevice(s->device));
+    const size_t N = size_t(s->dev.N);
+    const double* drho = rho;
+    const double* du = u;
+    double* tmp = nullptr;
+    if (!on_device) {
+        LBM_CK(cudaMallocAsync(&tmp, (1 + s->d) * N * sizeof(double), s->stream));
+        LBM_CK(cudaMemcpyAsync(tmp, rho, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+        drho = tmp;
+        if (u) {
+            LBM_CK(cudaMemcpyAsync(tmp + N, u, s->d * N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+            du = tmp + N;
+        }
+    }
+    int rc = reset_usolve(s);
+    if (rc) return rc;
+    s->cur = 0;
+    s->steps = 0;
+    const int B = s->kt.block, G = nblocks(s->dev.N, B);
+    LBM_CK(launch(s, s->kt.init_eq, G, B, s->dev, drho, du, 0));
+    if (tmp) LBM_CK(cudaFreeAsync(tmp, s->stream));
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// One step with every kernel launched on its own and the u-solve loop driven
+// from the host (the same kernels and order as the graph).
+int step_direct(lbm_sim* s)
+{
+    DevSim& dv = s->dev;
+    const int B = s->kt.block, G = nblocks(dv.N, B);
+    const int pair = 0, no = 0, src = s->cur;
+    cudaGraphConditionalHandle h{};
+    LBM_CK(launch(s, s->kt.moments, G, B, dv, src, pair));
+    LBM_CK(launch(s, s->kt.force, G, B, dv));
+    LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
+    for (int it = 0; it < dv.maxit + 1; ++it) {
+        LBM_CK(launch_tiled(s, s->kt.sweep, s->kt.smem_sweep, dv, pair));
+        LBM_CK(launch(s, s->kt.us_ctl, 1, 1, dv, pair, h, no));
+        int running = 0;
+        LBM_CK(cudaMemcpyAsync(&running, &dv.us[0].running, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+        LBM_CK(cudaStreamSynchronize(s->stream));
+        if (!running) break;
+    }
+    LBM_CK(launch_tiled(s, s->kt.derivs, s->kt.smem_derivs, dv));
+    LBM_CK(launch_tiled(s, s->kt.collide, s->kt.smem_collide, dv, src));
+    s->cur ^= 1;
+    return LBM_OK;
+}
+
+bool direct_mode()
+{
+    const char* v = std::getenv("LBM_LAUNCH");
+    return v && std::strcmp(v, "direct") == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm_step(lbm_sim* s, int64_t nsteps)
+{
+    if (!s || nsteps < 0) return LBM_E_INVALID_ARG;
+    LBM_CK(cudaSetDevice(s->device));
+    if (direct_mode()) {
+        for (int64_t k = 0; k < nsteps; ++k) {
+            const int rc = step_direct(s);
+            if (rc) return rc;
+        }
+        s->steps += nsteps;
+        return LBM_OK;
+    }
+    int64_t n = nsteps;
+    while (n >= 2) {
+        LBM_CK(cudaGraphLaunch(s->two[s->cur].x, s->stream));
+        n -= 2;
+    }
+    if (n == 1) {
+        LBM_CK(cudaGraphLaunch(s->one[s->cur].x, s->stream));
+        s->cur ^= 1;
+    }
+    s->steps += nsteps;
+    return LBM_OK;
+}
+
+int lbm_sync(lbm_sim* s)
+{
+    if (!s) return LBM_E_INVALID_ARG;
+    LBM_CK(cudaSetDevice(s->device));
+    LBM_CK(cudaStreamSynchronize(s->stream));
+    int bits = 0;
+    int rc = read_status(s, &bits);
+    if (rc) return rc;
+    return status_code(bits);
+}
+
+int lbm_fields(lbm_sim* s, double* rho, double* u, int on_device)
+{
+    if (!s) return LBM_E_INVALID_ARG;
+    LBM_CK(cudaSetDevice(s->device));
+    int rc = run_fields(s);
+    if (rc) return rc;
+    const size_t N = size_t(s->dev.N);
+    const int B = s->kt.block, G = nblocks(s->dev.N, B);
+    double* drho = rho;
+    double* du = u;
+    double* tmp = nullptr;
+    if (!on_device && (rho || u)) {
+        LBM_CK(cudaMallocAsync(&tmp, (1 + s->d) * N * sizeof(double), s->stream));
+        drho = rho ? tmp : nullptr;
+        du = u ? tmp + N : nullptr;
+    }
+    LBM_CK(launch(s, s->kt.fields_out, G, B, s->dev, 1, drho, du));
+    if (tmp) {
+        if (rho) LBM_CK(cudaMemcpyAsync(rho, drho, N * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        if (u) LBM_CK(cudaMemcpyAsync(u, du, s->d * N * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+        LBM_CK(cudaFreeAsync(tmp, s->stream));
+    }
+    LBM_CK(cudaStreamSynchronize(s->stream));
+    int bits = 0;
+    rc = read_status(s, &bits);
+    if (rc) return rc;
+    return status_code(bits);
+}
+
+int lbm_populations(lbm_sim* s, double* out, int on_device)
+{
+    if (!s || !out) return LBM_E_INVALID_ARG;
+    LBM_CK(cudaSetDevice(s->device));
+    const size_t bytes = size_t(s->Q) * size_t(s->dev.N) * sizeof(double);
+    double* d = out;
+    if (!on_device) LBM_CK(cudaMallocAsync(&d, bytes, s->stream));
+    const int B = s->kt.block, G = nblocks(s->dev.N, B);
+    LBM_CK(launch(s, s->kt.pops_out, G, B, s->dev, s->cur, d));
+    if (!on_device) {
+        LBM_CK(cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, s->stream));
+        LBM_CK(cudaFreeAsync(d, s->stream));
+    }
+    LBM_CK(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+int lbm_set_populations(lbm_sim* s, const double* in, int on_device)
+{
+    if (!s || !in) return LBM_E_INVALID_ARG;
+    LBM_CK(cudaSetDevice(s->device));
+    const size_t bytes = size_t(s->Q) * size_t(s->dev.N) * sizeof(double);
+    const double* d = in;
+    double* tmp = nullptr;
+    if (!on_device) {
+        LBM_CK(cudaMallocAsync(&tmp, bytes, s->stream));
+        LBM_CK(cudaMemcpyAsync(tmp, in, bytes, cudaMemcpyHostToDevice, s->stream));
+        d = tmp;
+    }
+    int rc = reset_usolve(s);
+    if (rc) return rc;
+    s->cur = 0;
+    const int B = s->kt.block, G = nblocks(s->dev.N, B);
+    LBM_CK(launch(s, s->kt.pops_in, G, B, s->dev, d, 0));
+    if (tmp) LBM_CK(cudaFreeAsync(tmp, s->stream));
+    LBM_CK(cudaStreamSynchronize(s->stream));
+    return LBM_OK;
+}
+
+int lbm_stats_get(lbm_sim* s, lbm_stats* out)
+{
+    if (!s || !out) return LBM_E_INVALID_ARG;
+    LBM_CK(cudaSetDevice(s->device));
+    LBM_CK(launch(s, s->kt.red_partial, kRedGrid, kRedBlock, s->dev, s->cur, s->red_part));
+    LBM_CK(launch(s, s->kt.red_final, 1, kRedBlock, s->dev, (const double*)s->red_part, kRedGrid, s->red_out));
+    double sums[4];
+    UsolveState u;
+    int st = 0;
+    LBM_CK(cudaMemcpyAsync(sums, s->red_out, sizeof(sums), cudaMemcpyDeviceToHost, s->stream));
+    LBM_CK(cudaMemcpyAsync(&u, &s->dev.us[0], sizeof(u), cudaMemcpyDeviceToHost, s->stream));
+    LBM_CK(cudaMemcpyAsync(&st, s->dev.status, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+    LBM_CK(cudaStreamSynchronize(s->stream));
+    out->mass = sums[0];
+    out->mom[0] = sums[1];
+    out->mom[1] = sums[2];
+    out->mom[2] = sums[3];
+    out->steps = s->steps;
+    out->usolve_iters_last = u.iters_last;
+    out->usolve_iters_max = u.iters_max;
+    out->usolve_resid = u.resid_last;
+    out->status = st;
+    out->usolve_sweeps_total = u.sweeps_total;
+    return LBM_OK;
+}
+
+int lbm_profile(lbm_sim* s, int reps, double* ms_out, int n)
+{
+    if (!s || reps < 1 || !ms_out || n < 0) return LBM_E_INVALID_ARG;
+    LBM_CK(cudaSetDevice(s->device));
+    DevSim& dv = s->dev;
+    const int B = s->kt.block, G = nblocks(dv.N, B);
+    const int src = s->cur, pair = 1;
+    cudaEvent_t e0, e1;
+    LBM_CK(cudaEventCreate(&e0));
+    LBM_CK(cudaEventCreate(&e1));
+    // scratch u-solve pair starts from the run's j~; the collision writes the spare buffer
+    LBM_CK(launch(s, s->kt.copy_jt, G, B, dv));
+    const int zero = 0;
+    LBM_CK(cudaMemcpyAsync(&dv.us[1].cur, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    int rc = LBM_OK;
+    for (int k = 0; k < 5 && rc == LBM_OK; ++k) {
+        for (int r = 0; r <= reps && rc == LBM_OK; ++r) {
+            if (r == 1 && cudaEventRecord(e0, s->stream) != cudaSuccess) rc = LBM_E_CUDA;
+            cudaError_t e = cudaSuccess;
+            switch (k) {
+            case 0: e = launch(s, s->kt.moments, G, B, dv, src, pair); break;
+            case 1: e = launch(s, s->kt.force, G, B, dv); break;
+            case 2: e = launch_tiled(s, s->kt.sweep, s->kt.smem_sweep, dv, pair); break;
+            case 3: e = launch_tiled(s, s->kt.derivs, s->kt.smem_derivs, dv); break;
+            case 4: e = launch_tiled(s, s->kt.collide, s->kt.smem_collide, dv, src); break;
+            }
+            if (e != cudaSuccess) rc = LBM_E_CUDA;
+        }
+        if (rc == LBM_OK && cudaEventRecord(e1, s->stream) != cudaSuccess) rc = LBM_E_CUDA;
+        if (rc == LBM_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = LBM_E_CUDA;
+        float ms = 0.f;
+        if (rc == LBM_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = LBM_E_CUDA;
+        if (rc == LBM_OK && k < n) ms_out[k] = double(ms) / reps;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    (void)cudaGetLastError();
+    // the scratch residual accumulators were left mid-loop: clear them
+    UsolveState u1{};
+    if (rc == LBM_OK && cudaMemcpyAsync(&dv.us[1], &u1, sizeof(u1), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
+        rc = LBM_E_CUDA;
+    if (rc == LBM_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = LBM_E_CUDA;
+    return rc;
+}
+
+namespace {
+struct CkptHeader {
+    char magic[8];
+    int32_t lattice, storage, usize, Q;
+    int64_t dims[3];
+    int64_t steps;
+    double gamma, kappa, rho0;
+};
+}  // namespace
+
+int lbm_save(lbm_sim* s, const char* path)
+{
+    if (!s || !path) return LBM_E_INVALID_ARG;
+    LBM_CK(cudaSetDevice(s->device));
+    LBM_CK(cudaStreamSynchronize(s->stream));
+    const size_t N = size_t(s->dev.N);
+    const size_t pbytes = size_t(s->Q) * N * s->kt.ssize;
+    const size_t zbytes = N * s->kt.rsize;
+    const size_t jbytes = 3 * N * s->kt.usize;
+    std::vector<char> buf(pbytes + zbytes + jbytes);
+    UsolveState us[2];
+    LBM_CK(cudaMemcpy(us, s->dev.us, sizeof(us), cudaMemcpyDeviceToHost));
+    LBM_CK(cudaMemcpy(buf.data(), s->dev.pop[s->cur], pbytes, cudaMemcpyDeviceToHost));
+    if (zbytes) LBM_CK(cudaMemcpy(buf.data() + pbytes, s->dev.pop0[s->cur], zbytes, cudaMemcpyDeviceToHost));
+    LBM_CK(cudaMemcpy(buf.data() + pbytes + zbytes, s->dev.jt[0][us[0].cur], jbytes, cudaMemcpyDeviceToHost));
+    CkptHeader h{};
+    std::memcpy(h.magic, "LBM2PH01", 8);
+    h.lattice = s->lattice;
+    h.storage = s->prm.storage;
+    h.usize = int32_t(s->kt.usize);
+    h.Q = s->Q;
+    for (int k = 0; k < 3; ++k) h.dims[k] = s->dims[k];
+    h.steps = s->steps;
+    h.gamma = s->prm.gamma;
+    h.kappa = s->prm.kappa;
+    h.rho0 = s->prm.rho0;
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return LBM_E_IO;
+    bool ok = std::fwrite(&h, sizeof(h), 1, fp) == 1 && std::fwrite(&us[0], sizeof(UsolveState), 1, fp) == 1 &&
+              std::fwrite(buf.data(), 1, buf.size(), fp) == buf.size();
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? LBM_OK : LBM_E_IO;
+}
+
+int lbm_load(lbm_sim* s, const char* path)
+{
+    if (!s || !path) return LBM_E_INVALID_ARG;
+    LBM_CK(cudaSetDevice(s->device));
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return LBM_E_IO;
+    CkptHeader h{};
+    UsolveState u0{};
+    bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::fread(&u0, sizeof(u0), 1, fp) == 1;
+    ok = ok && std::memcmp(h.magic, "LBM2PH01", 8) == 0 && h.lattice == s->lattice && h.storage == s->prm.storage &&
+         h.usize == int32_t(s->kt.usize) && h.Q == s->Q && h.dims[0] == s->dims[0] && h.dims[1] == s->dims[1] &&
+         h.dims[2] == s->dims[2];
+    const size_t N = size_t(s->dev.N);
+    const size_t pbytes = size_t(s->Q) * N * s->kt.ssize;
+    const size_t zbytes = N * s->kt.rsize;
+    const size_t jbytes = 3 * N * s->kt.usize;
+    std::vector<char> buf;
+    if (ok) {
+        buf.resize(pbytes + zbytes + jbytes);
+        ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
+    }
+    std::fclose(fp);
+    if (!ok) return LBM_E_IO;
+    LBM_CK(cudaStreamSynchronize(s->stream));
+    int rc = reset_usolve(s);
+    if (rc) return rc;
+    s->cur = 0;
+    u0.cur = 0;
+    u0.resid_bits = 0;
+    u0.jmax_bits = 0;
+    LBM_CK(cudaMemcpy(s->dev.pop[0], buf.data(), pbytes, cudaMemcpyHostToDevice));
+    if (zbytes) LBM_CK(cudaMemcpy(s->dev.pop0[0], buf.data() + pbytes, zbytes, cudaMemcpyHostToDevice));
+    LBM_CK(cudaMemcpy(s->dev.jt[0][0], buf.data() + pbytes + zbytes, jbytes, cudaMemcpyHostToDevice));
+    LBM_CK(cudaMemcpy(&s->dev.us[0], &u0, sizeof(u0), cudaMemcpyHostToDevice));
+    s->steps = h.steps;
+    return LBM_OK;
+}
+
+int lbm_step_batch(lbm_sim* const* sims, int n, const int64_t* nsteps)
+{
+    if ((!sims || !nsteps) && n > 0) return LBM_E_INVALID_ARG;
+    for (int k = 0; k < n; ++k)
+        if (!sims[k] || nsteps[k] < 0) return LBM_E_INVALID_ARG;
+    for (int k = 0; k < n; ++k) {
+        int rc = lbm_step(sims[k], nsteps[k]);
+        if (rc) return rc;
+    }
+    return LBM_OK;
+}
+
+}  // extern "C"

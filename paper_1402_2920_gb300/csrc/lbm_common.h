@@ -1,0 +1,99 @@
+// Host/device shared declarations of the CUDA library: the parameter block
+// every kernel receives by value, the device-resident u-solve control word,
+// and the kernel table each lattice translation unit exports.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace lbm {
+
+enum Store { ST_F32 = 0, ST_F32_DEV = 1, ST_F16_DEV = 2, ST_BF16_DEV = 3, ST_F64 = 4 };
+
+// Device-resident state of one implicit u-solve (Sec. IX): which of the two
+// j~ buffers is current, the sweep counter and the residual reductions.
+struct UsolveState {
+    unsigned long long resid_bits;  // atomicMax over |j~new - j~| (non-negative double bits)
+    unsigned long long jmax_bits;   // atomicMax over |j~new|
+    int cur;                        // buffer holding the current j~
+    int iter;                       // sweeps of the solve in progress
+    int iters_last;                 // sweeps of the last finished solve
+    int iters_max;                  // largest sweep count since init
+    double resid_last;              // final residual of the last finished solve
+    int converged;                  // 1 once the last solve met its tolerance
+    int running;                    // 1 from k_us_begin until the control kernel stops the loop
+    long long sweeps_total;         // sweeps since the last reset
+};
+
+// Launch shape of the FP64 conservation sums (fixed, so the reduction order is fixed).
+constexpr int kRedBlock = 256;
+constexpr int kRedGrid = 1024;
+
+// Error bits recorded by kernels (read back by lbm_sync and friends).
+enum StatusBits { STB_WEIGHTS = 1, STB_NONFINITE_RHO = 2, STB_USOLVE_CAP = 4, STB_USOLVE_NAN = 8 };
+
+// Everything a kernel needs, passed by value (lives in the kernel parameter space).
+struct DevSim {
+    int lattice, d, Q;
+    int nx, ny, nz;
+    long long N;          // sites
+    // fields
+    void* pop[2];         // populations, [Q][N] in the storage type
+    void* pop0[2];        // float2 [N]: the rest population of the reduced storages as a float
+                          // pair hi + lo; unused for FP64 storage
+    void* rho_lo;         // float [N]: rho - rho0 minus its float rounding (reduced storages)
+    void* rho;            // T [N]: rho - rho0 (exact differences; rho0 + it recovers rho)
+    void* j0p;            // T [3][N]: j0 after S1, j0' = j0 + f/2 after S2
+    void* f;              // T [3][N]: interface force
+    void* jt[2][2];       // U [3][N]: j~ ping-pong buffers of pair 0 (the run) and pair 1 (lbm_fields)
+    void* q;              // U [6][N]: symmetric q_ab of the u-solve (S4)
+    void* aux;            // T [26][N]: A, B_ab, C_a, the local part of Sigma_ab, Xi'_abc
+    UsolveState* us;      // [2]: pair 0 and pair 1
+    int* status;          // error bits
+    double* red;          // reduction scratch
+    // physics
+    double gamma, kappa, rho0, cs0;  // cs0 = c_s^2(rho0)
+    double w0[8];                    // w_k(c_s^2(rho0)) per shell
+    double off[8];                   // w_k(c_s^2(rho0)) rho0: offsets of the deviation storages
+    int eos_kind;
+    double a, b, T;
+    double rho1, rho2, A, cs2_1;
+    double cs2_lo, cs2_hi;           // positive-weight window (Sec. III)
+    double tol, rtol;
+    double omega;                    // relaxation of the u-solve sweep (1 = the plain iteration)
+    int maxit, warm;
+};
+
+// Kernels of one (lattice, arithmetic, storage, u-solve arithmetic) combination.
+struct KernelTable {
+    const void* moments;      // (DevSim, int src, int pair)
+    const void* force;        // (DevSim)
+    const void* us_begin;     // (DevSim, int pair)
+    const void* sweep;        // (DevSim, int pair): one tiled u-solve sweep
+    const void* us_ctl;       // (DevSim, int pair, cudaGraphConditionalHandle, int use_cond)
+    const void* derivs;       // (DevSim)
+    const void* collide;      // (DevSim, int src)
+    const void* init_eq;      // (DevSim, const double* rho, const double* u, int dst)
+    const void* fields_out;   // (DevSim, int pair, double* rho, double* u)
+    const void* pops_out;     // (DevSim, int src, double* out)
+    const void* pops_in;      // (DevSim, const double* in, int dst)
+    const void* red_partial;  // (DevSim, int src, double* partials)
+    const void* red_final;    // (DevSim, const double* partials, int nparts, double* out)
+    const void* copy_jt;      // (DevSim) copy pair-0 current j~ into pair-1 buffer 0
+    int block;                // threads per block of the per-site kernels
+    int tile[3];              // TX, TY, ZB of the tiled kernels
+    int tile_threads;
+    size_t smem_sweep, smem_derivs, smem_collide;  // dynamic shared memory bytes
+    size_t tsize, usize, ssize;  // bytes of T, U and the storage type
+    size_t rsize;                // bytes of a rest-plane element (0: no separate plane)
+    bool exact;                  // FP64 density bookkeeping (rho_lo is used)
+};
+
+// Exported by the lattice translation units.
+// read_pops: the collision needs the pre-collision populations (gamma != 0).
+bool get_kernels_d2q21(int storage, bool usolve_f64, bool read_pops, KernelTable* out);
+bool get_kernels_d3q59(int storage, bool usolve_f64, bool read_pops, KernelTable* out);
+
+}  // namespace lbm

@@ -1,0 +1,1231 @@
+// Device code of the two-phase lattice Boltzmann step (Zelko & Duenweg,
+// arXiv:1402.2920): lattice traits, equation of state, storage codecs and the
+// per-site kernels of the Supplemental Material's steps S1-S12.
+//
+// Kernel map (each is a full sweep, as the supplement requires between steps):
+//   k_moments   S1      rho = sum n_i, j0 = sum n_i c_i, c_s^2 window check
+//   k_force     S2      f = kappa rho d_a d_b d_b rho (Sec. IV.E), j0' = j0 + f/2
+//   k_sweep     S3-S6   one Jacobi sweep of the u-solve, tiled: u = (j0' + j~)/rho,
+//                       d_a u_b (Sec. IV.B), q_ab, j~new = -(1/12) d_b q_ab, max|j~new - j~|
+//   k_us_ctl    S6, S7  convergence test, buffer swap, graph loop condition
+//   k_derivs    S8-S11  u, j; first derivatives (tiled); A, B, C; the site-local
+//                       parts of Sigma and the whole Xi'
+//   k_collide   S11,S12 nested derivatives (tiled), Sigma, per-velocity collision,
+//                       push streaming n_i(r + c_i) = n_i + Delta_i
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
+#include "lbm_common.h"
+#include "lbm_lattice.h"
+
+namespace lbm {
+
+template <int LAT, typename T>
+__device__ __forceinline__ T weight(int k, T s)
+{
+    using L = Lat<LAT>;
+    return T(L::wc(k, 0)) + s * (T(L::wc(k, 1)) + s * (T(L::wc(k, 2)) + s * T(L::wc(k, 3))));
+}
+
+// ---------------------------------------------------------------------------
+// Storage codecs.  raw() returns what is stored: n_i, or n_i - w_i(rho0) rho0
+// for the deviation formats.  In the reduced storages (EXACT) the rest
+// population (i = 0) lives in a plane of its own as an unevaluated float pair
+// hi + lo, and the density sum is accumulated as a float pair with the
+// error-free TwoSum: the collision gives the rest population the exact mass
+// remainder, so the stored populations keep the pre-collision mass to about
+// 2^-48 relative (in plain float the same rounding repeats at every
+// stationary site and the mass drifts).
+// ---------------------------------------------------------------------------
+
+// s + e = a + b exactly (Knuth's TwoSum; the _rn intrinsics forbid contraction)
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (hi, lo) += v with the rounding error of the leading sum kept in lo
+__device__ __forceinline__ void acc2(float& hi, float& lo, float v)
+{
+    float e;
+    two_sum(hi, v, hi, e);
+    lo = __fadd_rn(lo, e);
+}
+template <int S>
+struct Codec;
+template <>
+struct Codec<ST_F32> {
+    using type = float;
+    static constexpr bool DEV = false, SPLIT0 = true, EXACT = true;
+    template <typename T>
+    __device__ static T raw(const type* p, long long k) { return T(p[k]); }
+    template <typename T>
+    __device__ static void put(type* p, long long k, T v) { p[k] = float(v); }
+    template <typename T>
+    __device__ static T rounded(T v) { return T(float(v)); }
+};
+template <>
+struct Codec<ST_F32_DEV> {
+    using type = float;
+    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true;
+    template <typename T>
+    __device__ static T raw(const type* p, long long k) { return T(p[k]); }
+    template <typename T>
+    __device__ static void put(type* p, long long k, T v) { p[k] = float(v); }
+    template <typename T>
+    __device__ static T rounded(T v) { return T(float(v)); }
+};
+template <>
+struct Codec<ST_F16_DEV> {
+    using type = __half;
+    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true;
+    template <typename T>
+    __device__ static T raw(const type* p, long long k) { return T(__half2float(p[k])); }
+    template <typename T>
+    __device__ static void put(type* p, long long k, T v) { p[k] = __float2half_rn(float(v)); }
+    template <typename T>
+    __device__ static T rounded(T v) { return T(__half2float(__float2half_rn(float(v)))); }
+};
+template <>
+struct Codec<ST_BF16_DEV> {
+    using type = __nv_bfloat16;
+    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true;
+    template <typename T>
+    __device__ static T raw(const type* p, long long k) { return T(__bfloat162float(p[k])); }
+    template <typename T>
+    __device__ static void put(type* p, long long k, T v) { p[k] = __float2bfloat16_rn(float(v)); }
+    template <typename T>
+    __device__ static T rounded(T v) { return T(__bfloat162float(__float2bfloat16_rn(float(v)))); }
+};
+template <>
+struct Codec<ST_F64> {
+    using type = double;
+    static constexpr bool DEV = false, SPLIT0 = false, EXACT = false;
+    template <typename T>
+    __device__ static T raw(const type* p, long long k) { return T(p[k]); }
+    template <typename T>
+    __device__ static void put(type* p, long long k, T v) { p[k] = double(v); }
+    template <typename T>
+    __device__ static T rounded(T v) { return T(double(v)); }
+};
+
+// ---------------------------------------------------------------------------
+// Equation of state (App. B; S1).  P = p, DP = dp/drho, PM = p - rho dp/drho,
+// RPP = rho d2p/drho2.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void eos_full(const DevSim& p, T rho, T& P, T& DP, T& PM, T& RPP)
+{
+    if (p.eos_kind == 0) {
+        const T g = T(1) - T(p.b) * rho;
+        const T ig = T(1) / g;
+        P = rho * T(p.T) * ig - T(p.a) * rho * rho;
+        DP = T(p.T) * ig * ig - T(2) * T(p.a) * rho;
+        RPP = rho * (T(2) * T(p.b) * T(p.T) * ig * ig * ig - T(2) * T(p.a));
+    } else {
+        const T D = T(p.rho2) - T(p.rho1);
+        const T rho3 = T(2) * T(p.rho2) - T(p.rho1);
+        T psi = T(0), dpsi = T(0), integ = T(0);
+        if (rho > T(p.rho1) && rho < rho3) {
+            const T ph = T(3.14159265358979323846) * (rho - T(p.rho1)) / D;
+            const T sn = sin(ph), cn = cos(ph);
+            psi = T(p.A) * sn;
+            dpsi = T(p.A) * T(3.14159265358979323846) / D * cn;
+            integ = T(p.A) * D / T(3.14159265358979323846) * (T(1) - cn);
+        }
+        const T cs2 = T(p.cs2_1) * exp(integ);
+        P = rho * cs2;
+        DP = cs2 * (T(1) + rho * psi);
+        RPP = rho * (cs2 * psi * (T(1) + rho * psi) + cs2 * (psi + rho * dpsi));
+    }
+    PM = P - rho * DP;
+}
+
+template <typename T>
+__device__ __forceinline__ T eos_p(const DevSim& p, T rho)
+{
+    T P, DP, PM, RPP;
+    eos_full(p, rho, P, DP, PM, RPP);
+    return P;
+}
+
+// c_s^2 = p/rho at rho = rho0 + drho, and its difference ds from c_s^2(rho0) = cs0,
+// evaluated from drho directly so that ds keeps its relative precision when small.
+template <typename T>
+__device__ __forceinline__ void cs2_delta(const DevSim& p, T drho, T& s, T& ds)
+{
+    const T rho = T(p.rho0) + drho;
+    if (p.eos_kind == 0) {
+        // s = T/(1 - b rho) - a rho  =>  s - s0 = drho (T b / ((1 - b rho)(1 - b rho0)) - a)
+        const T g = T(1) - T(p.b) * rho, g0 = T(1.0 - p.b * p.rho0);
+        s = T(p.T) / g - T(p.a) * rho;
+        ds = drho * (T(p.T) * T(p.b) / (g * g0) - T(p.a));
+    } else {
+        // s = cs2(rho1) exp(I), I = (A D / pi)(1 - cos phi), phi = pi (rho - rho1)/D clamped to [0, 2 pi]
+        const T D = T(p.rho2) - T(p.rho1);
+        const T PI = T(3.14159265358979323846);
+        const T ph_raw = PI * (rho - T(p.rho1)) / D, ph0_raw = T(M_PI * (p.rho0 - p.rho1) / (p.rho2 - p.rho1));
+        const T ph = fmin(fmax(ph_raw, T(0)), T(2) * PI), ph0 = fmin(fmax(ph0_raw, T(0)), T(2) * PI);
+        const bool inside = ph == ph_raw && ph0 == ph0_raw;
+        const T dph = inside ? PI * drho / D : ph - ph0;
+        const T dI = T(p.A) * D / PI * T(2) * sin(T(0.5) * (ph + ph0)) * sin(T(0.5) * dph);
+        const T s0 = T(p.cs0);
+        ds = s0 * expm1(dI);
+        s = s0 + ds;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Periodic neighbourhoods.  Every extent is >= 4, so one correction wraps any
+// shift of at most 4.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int wrapc(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+struct Site {
+    int x, y, z;
+    long long s;
+};
+
+__device__ __forceinline__ Site site_of(const DevSim& p, long long s)
+{
+    Site r;
+    r.s = s;
+    r.x = int(s % p.nx);
+    long long t = s / p.nx;
+    r.y = int(t % p.ny);
+    r.z = int(t / p.ny);
+    return r;
+}
+
+__device__ __forceinline__ long long at(const DevSim& p, int x, int y, int z)
+{
+    return (long long)x + (long long)p.nx * ((long long)y + (long long)p.ny * z);
+}
+
+__device__ __forceinline__ long long shifted(const DevSim& p, const Site& r, int dx, int dy, int dz)
+{
+    return at(p, wrapc(r.x + dx, p.nx), wrapc(r.y + dy, p.ny), wrapc(r.z + dz, p.nz));
+}
+
+// Site indices of r - 2e_a, r - e_a, r + e_a, r + 2e_a for every axis a.
+struct Axes {
+    long long n[3][4];
+};
+
+template <int D>
+__device__ __forceinline__ void make_axes(const DevSim& p, const Site& r, Axes& A)
+{
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const int sh[4] = {-2, -1, 1, 2};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            A.n[a][k] = shifted(p, r, a == 0 ? sh[k] : 0, a == 1 ? sh[k] : 0, a == 2 ? sh[k] : 0);
+    }
+}
+
+// First derivative of Sec. IV.B along axis a: shells (1 0) with 2/3 and (2 0)
+// with -1/24, i.e. (2/3)(g(+1) - g(-1)) - (1/12)(g(+2) - g(-2)).
+template <typename T, class G>
+__device__ __forceinline__ T d1(const Axes& A, int a, G g)
+{
+    return T(2.0 / 3.0) * (g(A.n[a][2]) - g(A.n[a][1])) - T(1.0 / 12.0) * (g(A.n[a][3]) - g(A.n[a][0]));
+}
+
+// symmetric-pair index in 2D (xx, yy, xy) and 3D (xx, yy, zz, xy, xz, yz)
+template <int D>
+__host__ __device__ __forceinline__ constexpr int sym2(int a, int b)
+{
+    if (a == b) return a;
+    if (D == 2) return 2;
+    const int lo = a < b ? a : b, hi = a < b ? b : a;
+    return lo == 0 ? (hi == 1 ? 3 : 4) : 5;
+}
+// fully symmetric 3-index: 2D (xxx, yyy, xxy, xyy); 3D (xxx, yyy, zzz, xxy, xxz, xyy, yyz, xzz, yzz, xyz)
+template <int D>
+__host__ __device__ __forceinline__ constexpr int sym3(int a, int b, int c)
+{
+    const int nx = (a == 0) + (b == 0) + (c == 0);
+    const int ny = (a == 1) + (b == 1) + (c == 1);
+    const int nz = (a == 2) + (b == 2) + (c == 2);
+    if (D == 2) return nx == 3 ? 0 : ny == 3 ? 1 : nx == 2 ? 2 : 3;
+    if (nx == 3) return 0;
+    if (ny == 3) return 1;
+    if (nz == 3) return 2;
+    if (nx == 2) return ny == 1 ? 3 : 4;
+    if (ny == 2) return nx == 1 ? 5 : 6;
+    if (nz == 2) return nx == 1 ? 7 : 8;
+    return 9;
+}
+
+// aux layout offsets
+template <int D>
+struct AuxLayout {
+    static constexpr int NB = D == 2 ? 3 : 6;
+    static constexpr int NX = D == 2 ? 4 : 10;
+    static constexpr int A = 0, B = 1, C = 1 + NB, SIGL = 1 + NB + D, XI = 1 + NB + D + NB;
+    static constexpr int N = XI + NX;
+};
+
+__device__ __forceinline__ long long gtid() { return blockIdx.x * (long long)blockDim.x + threadIdx.x; }
+
+template <typename T>
+__device__ __forceinline__ const T* cp(const void* v) { return static_cast<const T*>(v); }
+template <typename T>
+__device__ __forceinline__ T* mp(void* v) { return static_cast<T*>(v); }
+
+// Stored value of population i at site s of buffer b: n_i, or n_i - w_i(rho0) rho0.
+// The 16-bit storages keep the rest population (i = 0) in FP32 so that the mass
+// remainder below survives storage.
+template <int S, typename T>
+__device__ __forceinline__ T pop_raw(const DevSim& p, int b, int i, long long s)
+{
+    using C = Codec<S>;
+    if (C::SPLIT0 && i == 0) {
+        const float2 r = cp<float2>(p.pop0[b])[s];
+        return T(r.x) + T(r.y);
+    }
+    return C::template raw<T>(cp<typename C::type>(p.pop[b]), (long long)i * p.N + s);
+}
+
+// Store v (in the storage's convention) and return the value actually stored.
+template <int S, typename T>
+__device__ __forceinline__ T pop_put(const DevSim& p, int b, int i, long long s, T v)
+{
+    using C = Codec<S>;
+    if (C::SPLIT0 && i == 0) {
+        const float hi = float(v);
+        const float lo = float(v - T(hi));
+        mp<float2>(p.pop0[b])[s] = make_float2(hi, lo);
+        return T(hi) + T(lo);
+    }
+    C::template put<T>(mp<typename C::type>(p.pop[b]), (long long)i * p.N + s, v);
+    return C::template rounded<T>(v);
+}
+
+// block-wide maximum of two non-negative doubles, then atomicMax on their bit patterns
+__device__ __forceinline__ void block_max2(double a, double b, unsigned long long* da, unsigned long long* db)
+{
+    __shared__ double sa[32], sb[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    // NaN must win: fmax drops it, so fold a NaN flag separately
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { sa[warp] = a; sb[warp] = b; }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        a = lane < nw ? sa[lane] : 0.0;
+        b = lane < nw ? sb[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+            b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+        }
+        if (lane == 0) {
+            atomicMax(da, (unsigned long long)__double_as_longlong(a));
+            atomicMax(db, (unsigned long long)__double_as_longlong(b));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// S1: moments and the c_s^2 window check
+// ---------------------------------------------------------------------------
+template <int LAT, typename T, int S, typename U>
+__global__ void k_moments(DevSim p, int src, int pair)
+{
+    using L = Lat<LAT>;
+    using C = Codec<S>;
+    const long long s = gtid();
+    if (s >= p.N) return;
+    T sum = T(0), j[3] = {T(0), T(0), T(0)};
+    float hi = 0.f, lo = 0.f;
+    if (C::EXACT) {
+        const float2 r0 = cp<float2>(p.pop0[src])[s];
+        hi = r0.x;
+        lo = r0.y;
+    }
+#pragma unroll
+    for (int i = C::EXACT ? 1 : 0; i < L::Q; ++i) {
+        const T v = pop_raw<S, T>(p, src, i, s);
+        if (C::EXACT) acc2(hi, lo, float(v));
+        else sum += v;
+        if (L::cx(i)) j[0] += T(L::cx(i)) * v;
+        if (L::cy(i)) j[1] += T(L::cy(i)) * v;
+        if (L::cz(i)) j[2] += T(L::cz(i)) * v;
+    }
+    // rho - rho0: the deviation sum itself (sum_i w_i(rho0) rho0 = rho0 and the
+    // odd offsets cancel in j0), or sum - rho0
+    T drho;
+    if (C::EXACT) {
+        if (!C::DEV) {
+            float e;
+            two_sum(hi, -float(p.rho0), hi, e);
+            lo = __fadd_rn(lo, e);
+        }
+        float e;
+        two_sum(hi, lo, hi, e);  // renormalise: hi = the float nearest to the pair
+        drho = T(hi);
+        mp<float>(p.rho_lo)[s] = e;  // the part float drops
+    } else {
+        drho = C::DEV ? sum : sum - T(p.rho0);
+    }
+    const T r = T(p.rho0) + drho;
+    mp<T>(p.rho)[s] = drho;
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) mp<T>(p.j0p)[a * p.N + s] = j[a];
+    if (!p.warm) {
+        U* jt = mp<U>(p.jt[pair][p.us[pair].cur]);
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) jt[a * p.N + s] = U(0);
+    }
+    const T cs2 = eos_p(p, r) / r;
+    if (!isfinite(r)) atomicOr(p.status, STB_NONFINITE_RHO);
+    else if (!(cs2 > T(p.cs2_lo) && cs2 < T(p.cs2_hi))) atomicOr(p.status, STB_WEIGHTS);
+}
+
+// ---------------------------------------------------------------------------
+// S2: interface force (Sec. VI with the third-derivative stencil of Sec. IV.E)
+// ---------------------------------------------------------------------------
+template <int LAT, typename T>
+__global__ void k_force(DevSim p)
+{
+    using L = Lat<LAT>;
+    const long long s = gtid();
+    if (s >= p.N) return;
+    const Site r = site_of(p, s);
+    const T* drho = cp<T>(p.rho);
+    auto R = [&](int dx, int dy, int dz) { return drho[shifted(p, r, dx, dy, dz)]; };  // rho - rho0
+    T f[3];
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) {
+        const int ex = a == 0, ey = a == 1, ez = a == 2;
+        const T ax = R(ex, ey, ez) - R(-ex, -ey, -ez);
+        const T two = R(2 * ex, 2 * ey, 2 * ez) - R(-2 * ex, -2 * ey, -2 * ez);
+        T diag = T(0);
+#pragma unroll
+        for (int b = 0; b < L::D; ++b) {
+            if (b == a) continue;
+            const int bx = b == 0, by = b == 1, bz = b == 2;
+#pragma unroll
+            for (int sg = -1; sg <= 1; sg += 2)
+                diag += R(ex + sg * bx, ey + sg * by, ez + sg * bz) - R(-ex + sg * bx, -ey + sg * by, -ez + sg * bz);
+        }
+        // sum_i tau_i d_ia rho(r + d_i): the (2 0) shell has d_a = +-2
+        const T lap3 = T(L::T3_AX) * ax + T(L::T3_DIAG) * diag + T(2.0 * L::T3_TWO) * two;
+        f[a] = T(p.kappa) * (T(p.rho0) + drho[s]) * lap3;
+    }
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) {
+        mp<T>(p.f)[a * p.N + s] = f[a];
+        mp<T>(p.j0p)[a * p.N + s] += T(0.5) * f[a];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// S3-S7: the implicit u-solve (Sec. IX)
+// ---------------------------------------------------------------------------
+static __global__ void k_us_begin(DevSim p, int pair)
+{
+    UsolveState& u = p.us[pair];
+    u.iter = 0;
+    u.resid_bits = 0ull;
+    u.jmax_bits = 0ull;
+    u.converged = 0;
+    u.running = 1;
+}
+
+// One thread: the S6 test, the S7 swap, and the loop condition of the graph.
+static __global__ void k_us_ctl(DevSim p, int pair, cudaGraphConditionalHandle h, int use_cond)
+{
+    UsolveState& u = p.us[pair];
+    const double r = __longlong_as_double((long long)u.resid_bits);
+    const double jm = __longlong_as_double((long long)u.jmax_bits);
+    u.iter += 1;
+    u.sweeps_total += 1;
+    u.cur ^= 1;
+    const bool bad = !isfinite(r);
+    const bool conv = !bad && r <= p.tol + p.rtol * jm;
+    const bool stop = conv || bad || u.iter >= p.maxit;
+    if (bad) atomicOr(p.status, STB_USOLVE_NAN);
+    else if (stop && !conv) atomicOr(p.status, STB_USOLVE_CAP);
+    u.resid_bits = 0ull;
+    u.jmax_bits = 0ull;
+    if (stop) {
+        u.iters_last = u.iter;
+        u.iters_max = u.iter > u.iters_max ? u.iter : u.iters_max;
+        u.resid_last = r;
+        u.converged = conv ? 1 : 0;
+        u.running = 0;
+    }
+    if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
+}
+
+// ---------------------------------------------------------------------------
+// Per-site tails shared by the tiled kernels below
+// ---------------------------------------------------------------------------
+template <int LAT, typename T>
+__device__ __forceinline__ void collision_consts(const DevSim& p, T& k1, T& k2, T& k3)
+{
+    const double g = p.gamma;
+    k1 = T(-0.25 * (g + 1.0) * (g + 1.0) / (g - 1.0));       // -(h^2/4)(g+1)^2/(g-1)
+    k2 = T((1.0 / 6.0) * (g * g + 4.0 * g + 1.0) / (g - 1.0));  // (h^2/6)(g^2+4g+1)/(g-1)
+    k3 = T((1.0 / 3.0) * (g * g + 4.0 * g + 1.0) / (g + 1.0));  // (h/3)(g^2+4g+1)/(g+1)
+}
+
+// S10 results at one site -> A = (p - rho p') div u, B_ab = p(d_a u_b + d_b u_a),
+// C_b = rho^-1 d_b p + u_g d_g u_b (the three bracketed S11 arguments), the
+// site-local part of Sigma and the whole Xi' (S11), written to aux.
+template <int LAT, typename T>
+__device__ __forceinline__ void derivs_tail(const DevSim& p, long long s, const T (&du)[3][3], T divj,
+                                            const T (&dp)[3], const T (&dpr)[3], const T (&dpuu)[3][3][3], T rs,
+                                            const T (&u)[3], const T (&jtl)[3])
+{
+    constexpr int D = Lat<LAT>::D;
+    using AL = AuxLayout<D>;
+    T P, DP, PM, RPP;
+    eos_full<T>(p, rs, P, DP, PM, RPP);
+    T divu = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) divu += du[a][a];
+    T k1, k2, k3;
+    collision_consts<LAT, T>(p, k1, k2, k3);
+    T* aux = mp<T>(p.aux);
+    aux[AL::A * p.N + s] = PM * divu;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = a; b < D; ++b) {
+            const T sd = du[a][b] + du[b][a];
+            aux[(AL::B + sym2<D>(a, b)) * p.N + s] = P * sd;
+            aux[(AL::SIGL + sym2<D>(a, b)) * p.N + s] = k2 * (-DP * divj * sd + (a == b ? RPP * divu * divj : T(0)));
+        }
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+        T c = dp[b] / rs;
+#pragma unroll
+        for (int g = 0; g < D; ++g) c += u[g] * du[g][b];
+        aux[(AL::C + b) * p.N + s] = c;
+    }
+    // Xi'_abc = k3 [X(a,b;c) + X(a,c;b) + X(b,c;a)] + (1-gamma) cs0 (delta j~ sym),
+    // X(a,b;c) = d_c(p u_a u_b) + delta_ab [p d_c(p/rho) + (p - rho p') u_c div u]
+    auto PUU = [&](int c, int a, int b) { return a <= b ? dpuu[c][a][b] : dpuu[c][b][a]; };
+    auto X = [&](int a, int b, int c) { return PUU(c, a, b) + (a == b ? P * dpr[c] + PM * u[c] * divu : T(0)); };
+    const T cj = T((1.0 - p.gamma) * p.cs0);
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int b = a; b < D; ++b)
+#pragma unroll
+            for (int c = b; c < D; ++c) {
+                T v = k3 * (X(a, b, c) + X(a, c, b) + X(b, c, a));
+                v += cj * ((a == b ? jtl[c] : T(0)) + (a == c ? jtl[b] : T(0)) + (b == c ? jtl[a] : T(0)));
+                aux[(AL::XI + sym3<D>(a, b, c)) * p.N + s] = v;
+            }
+}
+
+// Collision of one site with Sigma and Xi' known, and push streaming (S11, S12).
+template <int LAT, typename T, int S, bool READ>
+__device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Site& r, T drs, const T (&u)[3],
+                                             const T (&f)[3], const T (&jtl)[3], const T (&Sig)[3][3],
+                                             const T (&Xi)[10])
+{
+    using L = Lat<LAT>;
+    using C = Codec<S>;
+    constexpr int D = L::D;
+    const long long s = r.s;
+    const T rs = T(p.rho0) + drs;
+    T cs2, dcs2;
+    cs2_delta<T>(p, drs, cs2, dcs2);
+    const T cs0 = T(p.cs0);
+    T trS = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) trS += Sig[a][a];
+    T trX[3];
+#pragma unroll
+    for (int b = 0; b < D; ++b) {
+        T t = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a) t += Xi[sym3<D>(a, a, b)];
+        trX[b] = t;
+    }
+    const T ics2 = T(1) / cs2;
+    T uu = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) uu += u[a] * u[a];
+    T wl[L::NSHELL], w0[L::NSHELL], dw0[L::NSHELL];
+#pragma unroll
+    for (int k = 0; k < L::NSHELL; ++k) {
+        wl[k] = weight<LAT, T>(k, cs2);
+        w0[k] = T(p.w0[k]);
+        // n^eq - w(rho0) rho0 = w rho X + w drho + rho0 (w(s) - w(s0)), and
+        // w(s) - w(s0) = (s - s0) [c1 + c2 (s + s0) + c3 (s^2 + s s0 + s0^2)]
+        dw0[k] = C::DEV ? wl[k] * drs + T(p.rho0) * dcs2 *
+                                           (T(Lat<LAT>::wc(k, 1)) + T(Lat<LAT>::wc(k, 2)) * (cs2 + cs0) +
+                                            T(Lat<LAT>::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0))
+                        : T(0);
+    }
+    const T g = T(p.gamma);
+    const T ics0 = T(1) / cs0;
+    const T cf_int = T(0.5 * (1.0 + p.gamma)) * ics0;
+    const T cf_jt = T(p.gamma - 1.0) * ics0;
+    const T cf_h2 = T(0.5) * ics0 * ics0;
+    const T cf_h3 = T(1.0 / 6.0) * ics0 * ics0 * ics0;
+    // wrapped destination offsets (site indices < 2^31) for the shifts -4, -2, -1, 0, 1, 2, 4
+    // that the velocity components take
+    int ox[7], oy[7], oz[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        const int sh = k == 0 ? -4 : k == 6 ? 4 : k - 3;
+        ox[k] = wrapc(r.x + sh, p.nx);
+        oy[k] = wrapc(r.y + sh, p.ny) * p.nx;
+        oz[k] = D == 3 ? wrapc(r.z + sh, p.nz) * p.nx * p.ny : 0;
+    }
+    auto sidx = [](int c) { return c == -4 ? 0 : c == 4 ? 6 : c + 3; };
+    // Every population but the rest one; the rest population then takes the
+    // remainder, so the stored populations sum to the pre-collision density
+    // (sum_i Delta_i = 0 holds exactly for the method's collision operator).
+    T stored_sum = T(0);
+    float sh = 0.f, sl = 0.f;  // float-pair sum of the stored values (EXACT storages)
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+        const int c[3] = {cx, cy, cz};
+        const int k = L::shell(i);
+        T uc = T(0), cf = T(0), cjt = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+            if (c[a]) { uc += T(c[a]) * u[a]; cf += T(c[a]) * f[a]; cjt += T(c[a]) * jtl[a]; }
+        T h2 = -cs0 * trS, h3 = T(0);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = 0; b < D; ++b)
+                if (c[a] && c[b]) h2 += Sig[a][b] * T(c[a] * c[b]);
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = 0; b < D; ++b)
+#pragma unroll
+                for (int cc = 0; cc < D; ++cc)
+                    if (c[a] && c[b] && c[cc]) h3 += Xi[sym3<D>(a, b, cc)] * T(c[a] * c[b] * c[cc]);
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+            if (c[b]) h3 -= T(3) * cs0 * trX[b] * T(c[b]);
+        const T X = uc * ics2 + T(0.5) * uc * uc * ics2 * ics2 - T(0.5) * uu * ics2;
+        // n^eq in the storage's convention: n^eq itself, or n^eq - w_i(rho0) rho0
+        const T neq = C::DEV ? wl[k] * rs * X + dw0[k] : wl[k] * rs * (T(1) + X);
+        const T dcorr = w0[k] * (cf_int * cf + cf_jt * cjt + cf_h2 * h2 + cf_h3 * h3);
+        // n* = gamma n + (1 - gamma) n^eq + Delta^int + Delta^corr; the offsets cancel in the deviation form
+        T nstar = (T(1) - g) * neq + dcorr;
+        if (READ) nstar += g * pop_raw<S, T>(p, src, i, s);
+        const long long dst = ox[sidx(cx)] + oy[sidx(cy)] + oz[sidx(cz)];
+        const T stored = pop_put<S, T>(p, src ^ 1, i, dst, nstar);
+        if (C::EXACT) acc2(sh, sl, float(stored));
+        else stored_sum += stored;
+    }
+    // rest population: the stored convention sums to rho - rho0 (deviations) or rho
+    if (C::EXACT) {
+        float th = float(drs), tl = cp<float>(p.rho_lo)[s];  // the exact pre-collision sum
+        if (!C::DEV) {
+            float e;
+            two_sum(th, float(p.rho0), th, e);
+            tl = __fadd_rn(tl, e);
+        }
+        float rh, e;
+        two_sum(th, -sh, rh, e);
+        const float rl = __fadd_rn(e, __fsub_rn(tl, sl));
+        float h2, l2;
+        two_sum(rh, rl, h2, l2);
+        mp<float2>(p.pop0[src ^ 1])[s] = make_float2(h2, l2);
+    } else {
+        pop_put<S, T>(p, src ^ 1, 0, s, (C::DEV ? drs : rs) - stored_sum);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Tiled kernels.  A CTA owns TX x TY columns of one z-slab and marches along z
+// (2.5D blocking): each plane it loads is kept in a shared-memory ring of 5
+// planes (the reach of the Sec. IV.B first derivative is 2), so x and y
+// derivatives read the current plane and z derivatives the ring.  In 2D the
+// ring is the single plane.
+// ---------------------------------------------------------------------------
+template <int D>
+struct Tile {
+    static constexpr int TX = 32, TY = D == 3 ? 8 : 16, ZB = D == 3 ? 32 : 1;
+    static constexpr int NZR = D == 3 ? 5 : 1;
+    static constexpr int THREADS = TX * TY;
+};
+
+template <int D>
+__device__ __forceinline__ int ring_slot(int z)
+{
+    return D == 3 ? (z + 40) % 5 : 0;
+}
+
+// Base pointers of the ring planes z-2 .. z+2 (D = 3) or of the single plane (D = 2).
+template <int D, typename T>
+__device__ __forceinline__ void ring_planes(T* ring, int plane_elems, int z, const T* (&pl)[5])
+{
+    if (D == 3) {
+        const int s0 = (z + 38) % 5;  // slot of plane z - 2 (z >= -8)
+#pragma unroll
+        for (int k = 0; k < 5; ++k) pl[k] = ring + ((s0 + k) % 5) * plane_elems;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) pl[k] = ring;
+    }
+}
+
+// First derivative of Sec. IV.B along axis a, (2/3)(g(+1) - g(-1)) - (1/12)(g(+2) - g(-2)),
+// of a field read by g(plane, index) at in-plane index i (row pitch PX) of the centre plane.
+template <typename T, class G>
+__device__ __forceinline__ T d1p(const T* const (&pl)[5], int a, int i, int PX, G g)
+{
+    if (a == 0)
+        return T(2.0 / 3.0) * (g(pl[2], i + 1) - g(pl[2], i - 1)) - T(1.0 / 12.0) * (g(pl[2], i + 2) - g(pl[2], i - 2));
+    if (a == 1)
+        return T(2.0 / 3.0) * (g(pl[2], i + PX) - g(pl[2], i - PX)) -
+               T(1.0 / 12.0) * (g(pl[2], i + 2 * PX) - g(pl[2], i - 2 * PX));
+    return T(2.0 / 3.0) * (g(pl[3], i) - g(pl[1], i)) - T(1.0 / 12.0) * (g(pl[4], i) - g(pl[0], i));
+}
+
+// S3-S6 fused: one Jacobi sweep of the u-solve.  Stage U (halo 4): u = (j0' + j~)/rho;
+// stage Q (halo 2): d_a u_b and q_ab; stage J (tile): j~new = -(1/12) d_b q_ab and the
+// S6 difference.  j~new = j~ + omega (J - j~) (omega = 1 is the plain iteration).
+template <int LAT, typename T, typename U>
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_sweep(DevSim p, int pair)
+{
+    using L = Lat<LAT>;
+    constexpr int D = L::D;
+    using TL = Tile<D>;
+    constexpr int TX = TL::TX, TY = TL::TY, NZR = TL::NZR;
+    constexpr int UX = TX + 8, UY = TY + 8, QX = TX + 4, QY = TY + 4;
+    constexpr int NQ = D == 3 ? 6 : 3;
+    constexpr int HZ = D == 3 ? 4 : 0;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    U* su = reinterpret_cast<U*>(smem_raw);  // [NZR][4][UY][UX]: u_x, u_y, u_z, rho - rho0
+    U* sq = su + NZR * 4 * UY * UX;          // [NZR][NQ][QY][QX]
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
+    const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
+    const T* drho = cp<T>(p.rho);
+    const T* j0p = cp<T>(p.j0p);
+    const int cur = p.us[pair].cur;
+    const U* jold = cp<U>(p.jt[pair][cur]);
+    U* jnew = mp<U>(p.jt[pair][cur ^ 1]);
+    const U omega = U(p.omega);
+    U dmax = U(0), jmax = U(0);  // residual reductions in the sweep's own precision
+    bool bad = false;
+    // stage U inputs of one plane, fetched one plane ahead into registers
+    constexpr int MU = (UX * UY + TL::THREADS - 1) / TL::THREADS;
+    T pr[MU], pj[MU][3];
+    U pt[MU][3];
+    auto fetch = [&](int zl) {
+        const int gz = D == 3 ? wrapc(zl, p.nz) : 0;
+#pragma unroll
+        for (int m = 0; m < MU; ++m) {
+            const int k = tid + m * nth;
+            if (k < UX * UY) {
+                const int ix = k % UX, iy = k / UX;
+                const long long g = at(p, wrapc(x0 - 4 + ix, p.nx), wrapc(y0 - 4 + iy, p.ny), gz);
+                pr[m] = drho[g];
+#pragma unroll
+                for (int a = 0; a < D; ++a) { pj[m][a] = j0p[a * p.N + g]; pt[m][a] = jold[a * p.N + g]; }
+            }
+        }
+    };
+    fetch(z0 - HZ);
+    for (int zl = z0 - HZ; zl < z1 + HZ; ++zl) {
+        {  // stage U: plane zl from the registers, then fetch the next plane
+            U* dst = su + ring_slot<D>(zl) * 4 * UY * UX;
+#pragma unroll
+            for (int m = 0; m < MU; ++m) {
+                const int k = tid + m * nth;
+                if (k < UX * UY) {
+                    const U dr = U(pr[m]);
+                    const U rho = U(p.rho0) + dr;
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) dst[a * UY * UX + k] = a < D ? (U(pj[m][a]) + pt[m][a]) / rho : U(0);
+                    dst[3 * UY * UX + k] = dr;
+                }
+            }
+            if (zl + 1 < z1 + HZ) fetch(zl + 1);
+        }
+        __syncthreads();
+        const int zq = zl - HZ / 2;
+        if (D == 2 || (zq >= z0 - 2 && zq < z1 + 2)) {  // stage Q: plane zq
+            const U* pl[5];
+            ring_planes<D, U>(su, 4 * UY * UX, zq, pl);
+            for (int k = tid; k < QX * QY; k += nth) {
+                const int qx = k % QX, qy = k / QX;
+                const int ui = (qy + 2) * UX + qx + 2;
+                U du[3][3];
+#pragma unroll
+                for (int b = 0; b < D; ++b)
+#pragma unroll
+                    for (int a = 0; a < D; ++a)
+                        du[a][b] = d1p<U>(pl, a, ui, UX, [&](const U* P, int j) { return P[b * UY * UX + j]; });
+                U P, DP, PM, RPP;
+                eos_full<U>(p, U(p.rho0) + pl[2][3 * UY * UX + ui], P, DP, PM, RPP);
+                U div = U(0);
+#pragma unroll
+                for (int a = 0; a < D; ++a) div += du[a][a];
+                U* dq = sq + ring_slot<D>(zq) * NQ * QY * QX;
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+#pragma unroll
+                    for (int b = a; b < D; ++b)
+                        dq[sym2<D>(a, b) * QY * QX + k] = (a == b ? PM * div : U(0)) + P * (du[b][a] + du[a][b]);
+            }
+        }
+        __syncthreads();
+        const int zj = zl - HZ;
+        if (zj >= z0 && zj < z1) {  // stage J: plane zj
+            const int gz = D == 3 ? zj : 0;
+            const U* ql[5];
+            ring_planes<D, U>(sq, NQ * QY * QX, zj, ql);
+            for (int k = tid; k < TX * TY; k += nth) {
+                const int ix = k % TX, iy = k / TX;
+                const int gx = x0 + ix, gy = y0 + iy;
+                if (gx >= p.nx || gy >= p.ny) continue;
+                const long long g = at(p, gx, gy, gz);
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    U acc = U(0);
+#pragma unroll
+                    for (int b = 0; b < D; ++b) {
+                        const int c = sym2<D>(a, b);
+                        acc += d1p<U>(ql, b, (iy + 2) * QX + ix + 2, QX, [&](const U* P, int j) { return P[c * QY * QX + j]; });
+                    }
+                    const U jt_old = jold[a * p.N + g];
+                    const U v = jt_old + omega * (-(U(1) / U(12)) * acc - jt_old);
+                    jnew[a * p.N + g] = v;
+                    const U dv = fabs(v - jt_old);
+                    bad |= !(dv == dv);
+                    dmax = fmax(dmax, dv);
+                    jmax = fmax(jmax, fabs(v));
+                }
+            }
+        }
+    }
+    // NaN -> +inf, which orders above every finite residual
+    const double dmax_d = bad ? __longlong_as_double(0x7ff0000000000000ll) : double(dmax);
+    block_max2(dmax_d, double(jmax), &p.us[pair].resid_bits, &p.us[pair].jmax_bits);
+}
+
+// S8 and S10 (tiled): the pointwise rho, u, p of every plane go to the ring
+// (halo 2); the first derivatives of u, j = rho u, p, p/rho and p u_b u_c
+// at the tile's sites feed derivs_tail.
+template <int LAT, typename T, typename U>
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim p)
+{
+    using L = Lat<LAT>;
+    constexpr int D = L::D;
+    using TL = Tile<D>;
+    constexpr int TX = TL::TX, TY = TL::TY;
+    constexpr int RX = TX + 4, RY = TY + 4, NP = 6;  // u_x, u_y, u_z, rho, p, p/rho
+    constexpr int HZ = D == 3 ? 2 : 0;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sr = reinterpret_cast<T*>(smem_raw);  // [NZR][NP][RY][RX]
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
+    const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
+    const T* drho = cp<T>(p.rho);
+    const T* j0p = cp<T>(p.j0p);
+    const U* jt = cp<U>(p.jt[0][p.us[0].cur]);
+    constexpr int MR = (RX * RY + TL::THREADS - 1) / TL::THREADS;
+    T pr[MR], pj[MR][3];
+    U pt[MR][3];
+    auto fetch = [&](int zl) {
+        const int gz = D == 3 ? wrapc(zl, p.nz) : 0;
+#pragma unroll
+        for (int m = 0; m < MR; ++m) {
+            const int k = tid + m * nth;
+            if (k < RX * RY) {
+                const int ix = k % RX, iy = k / RX;
+                const long long g = at(p, wrapc(x0 - 2 + ix, p.nx), wrapc(y0 - 2 + iy, p.ny), gz);
+                pr[m] = drho[g];
+#pragma unroll
+                for (int a = 0; a < D; ++a) { pj[m][a] = j0p[a * p.N + g]; pt[m][a] = jt[a * p.N + g]; }
+            }
+        }
+    };
+    fetch(z0 - HZ);
+    for (int zl = z0 - HZ; zl < z1 + HZ; ++zl) {
+        {
+            T* dst = sr + ring_slot<D>(zl) * NP * RY * RX;
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+                const int k = tid + m * nth;
+                if (k < RX * RY) {
+                    const T rho = T(p.rho0) + pr[m];
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) dst[a * RY * RX + k] = a < D ? (pj[m][a] + T(pt[m][a])) / rho : T(0);
+                    const T P = eos_p<T>(p, rho);
+                    dst[3 * RY * RX + k] = rho;
+                    dst[4 * RY * RX + k] = P;
+                    dst[5 * RY * RX + k] = P / rho;
+                }
+            }
+            if (zl + 1 < z1 + HZ) fetch(zl + 1);
+        }
+        __syncthreads();
+        const int zc = zl - HZ;
+        if (zc >= z0 && zc < z1) {
+            const int gz = D == 3 ? zc : 0;
+            const T* pl[5];
+            ring_planes<D, T>(sr, NP * RY * RX, zc, pl);
+            constexpr int PS = RY * RX;
+            for (int k = tid; k < TX * TY; k += nth) {
+                const int ix = k % TX, iy = k / TX;
+                const int gx = x0 + ix, gy = y0 + iy;
+                if (gx >= p.nx || gy >= p.ny) continue;
+                const int ri = (iy + 2) * RX + ix + 2;
+                T du[3][3], dp[3], dpr[3], dpuu[3][3][3];
+                T divj = T(0);
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+#pragma unroll
+                    for (int b = 0; b < D; ++b)
+                        du[a][b] = d1p<T>(pl, a, ri, RX, [&](const T* P, int j) { return P[b * PS + j]; });
+                    divj += d1p<T>(pl, a, ri, RX, [&](const T* P, int j) { return P[3 * PS + j] * P[a * PS + j]; });
+                    dp[a] = d1p<T>(pl, a, ri, RX, [&](const T* P, int j) { return P[4 * PS + j]; });
+                    dpr[a] = d1p<T>(pl, a, ri, RX, [&](const T* P, int j) { return P[5 * PS + j]; });
+#pragma unroll
+                    for (int b = 0; b < D; ++b)
+#pragma unroll
+                        for (int c = b; c < D; ++c)
+                            dpuu[a][b][c] = d1p<T>(pl, a, ri, RX, [&](const T* P, int j) {
+                                return P[4 * PS + j] * P[b * PS + j] * P[c * PS + j];
+                            });
+                }
+                const long long s = at(p, gx, gy, gz);
+                const T u[3] = {pl[2][ri], pl[2][PS + ri], pl[2][2 * PS + ri]};
+                T jtl[3] = {T(0), T(0), T(0)};
+#pragma unroll
+                for (int a = 0; a < D; ++a) jtl[a] = T(jt[a * p.N + s]);
+                derivs_tail<LAT, T>(p, s, du, divj, dp, dpr, dpuu, pl[2][3 * PS + ri], u, jtl);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// S11 (rest) and S12 (tiled): A, B, C of every plane go to the ring (halo 2);
+// d_a A, d_g B_ag and d_a C_b at the tile's sites complete Sigma; collide_tail
+// then collides and streams.
+template <int LAT, typename T, int S, typename U, bool READ>
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSim p, int src)
+{
+    using L = Lat<LAT>;
+    constexpr int D = L::D;
+    using AL = AuxLayout<D>;
+    using TL = Tile<D>;
+    constexpr int TX = TL::TX, TY = TL::TY;
+    constexpr int RX = TX + 4, RY = TY + 4, NP = 1 + AL::NB + D;  // A, B, C
+    constexpr int HZ = D == 3 ? 2 : 0;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sr = reinterpret_cast<T*>(smem_raw);  // [NZR][NP][RY][RX]
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
+    const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
+    const T* aux = cp<T>(p.aux);
+    const T* drho = cp<T>(p.rho);
+    const T* j0p = cp<T>(p.j0p);
+    const T* fp = cp<T>(p.f);
+    const U* jt = cp<U>(p.jt[0][p.us[0].cur]);
+    T k1, k2, k3;
+    collision_consts<LAT, T>(p, k1, k2, k3);
+    constexpr int MR = (RX * RY + TL::THREADS - 1) / TL::THREADS;
+    T pa[MR][NP];
+    auto fetch = [&](int zl) {
+        const int gz = D == 3 ? wrapc(zl, p.nz) : 0;
+#pragma unroll
+        for (int m = 0; m < MR; ++m) {
+            const int k = tid + m * nth;
+            if (k < RX * RY) {
+                const int ix = k % RX, iy = k / RX;
+                const long long g = at(p, wrapc(x0 - 2 + ix, p.nx), wrapc(y0 - 2 + iy, p.ny), gz);
+#pragma unroll
+                for (int c = 0; c < NP; ++c) pa[m][c] = aux[(AL::A + c) * p.N + g];
+            }
+        }
+    };
+    fetch(z0 - HZ);
+    for (int zl = z0 - HZ; zl < z1 + HZ; ++zl) {
+        {
+            T* dst = sr + ring_slot<D>(zl) * NP * RY * RX;
+#pragma unroll
+            for (int m = 0; m < MR; ++m) {
+                const int k = tid + m * nth;
+                if (k < RX * RY)
+#pragma unroll
+                    for (int c = 0; c < NP; ++c) dst[c * RY * RX + k] = pa[m][c];
+            }
+            if (zl + 1 < z1 + HZ) fetch(zl + 1);
+        }        __syncthreads();
+        const int zc = zl - HZ;
+        if (zc >= z0 && zc < z1) {
+            const int gz = D == 3 ? zc : 0;
+            const T* pl[5];
+            ring_planes<D, T>(sr, NP * RY * RX, zc, pl);
+            constexpr int PS = RY * RX;
+            for (int k = tid; k < TX * TY; k += nth) {
+                const int ix = k % TX, iy = k / TX;
+                const int gx = x0 + ix, gy = y0 + iy;
+                if (gx >= p.nx || gy >= p.ny) continue;
+                const int ri = (iy + 2) * RX + ix + 2;
+                Site r;
+                r.x = gx; r.y = gy; r.z = gz; r.s = at(p, gx, gy, gz);
+                const long long s = r.s;
+                const T drs = drho[s];
+                const T rs = T(p.rho0) + drs;
+                T u[3] = {T(0), T(0), T(0)}, f[3] = {T(0), T(0), T(0)}, jtl[3] = {T(0), T(0), T(0)};
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    jtl[a] = T(jt[a * p.N + s]);
+                    u[a] = (j0p[a * p.N + s] + jtl[a]) / rs;
+                    f[a] = fp[a * p.N + s];
+                }
+                T P, DP, PM, RPP;
+                eos_full<T>(p, rs, P, DP, PM, RPP);
+                T dA[3], divB[3], dC[3][3];
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    dA[a] = d1p<T>(pl, a, ri, RX, [&](const T* P, int j) { return P[j]; });
+                    T acc = T(0);
+#pragma unroll
+                    for (int g2 = 0; g2 < D; ++g2) {
+                        const int kb = 1 + sym2<D>(a, g2);
+                        acc += d1p<T>(pl, g2, ri, RX, [&](const T* P, int j) { return P[kb * PS + j]; });
+                    }
+                    divB[a] = acc;
+#pragma unroll
+                    for (int b = 0; b < D; ++b)
+                        dC[a][b] = d1p<T>(pl, a, ri, RX, [&](const T* P, int j) { return P[(1 + AL::NB + b) * PS + j]; });
+                }
+                T trdC = T(0);
+#pragma unroll
+                for (int a = 0; a < D; ++a) trdC += dC[a][a];
+                T Sig[3][3];
+#pragma unroll
+                for (int a = 0; a < D; ++a)
+#pragma unroll
+                    for (int b = a; b < D; ++b) {
+                        T v = k1 * (u[a] * (dA[b] + divB[b]) + u[b] * (dA[a] + divB[a]));
+                        v += k2 * (-P * (dC[a][b] + dC[b][a]) - (a == b ? PM * trdC : T(0)));
+                        v += aux[(AL::SIGL + sym2<D>(a, b)) * p.N + s];
+                        Sig[a][b] = v;
+                        Sig[b][a] = v;
+                    }
+                T Xi[10];
+#pragma unroll
+                for (int q = 0; q < AL::NX; ++q) Xi[q] = aux[(AL::XI + q) * p.N + s];
+                collide_tail<LAT, T, S, READ>(p, src, r, drs, u, f, jtl, Sig, Xi);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Initial condition, field and population transfer, conservation sums
+// ---------------------------------------------------------------------------
+template <int LAT, typename T, int S>
+__global__ void k_init_eq(DevSim p, const double* rho_in, const double* u_in, int dst)
+{
+    using L = Lat<LAT>;
+    using C = Codec<S>;
+    const long long s = gtid();
+    if (s >= p.N) return;
+    const T rs = T(rho_in[s]);
+    T u[3] = {T(0), T(0), T(0)};
+    if (u_in)
+#pragma unroll
+        for (int a = 0; a < L::D; ++a) u[a] = T(u_in[a * p.N + s]);
+    const T drs = T(rho_in[s] - p.rho0);
+    T cs2, dcs2;
+    cs2_delta<T>(p, drs, cs2, dcs2);
+    const T cs0 = T(p.cs0);
+    const T ics2 = T(1) / cs2;
+    T uu = T(0);
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) uu += u[a] * u[a];
+    double stored_sum = 0.0;  // initialisation is not on the hot path: FP64 is fine here
+#pragma unroll
+    for (int i = 1; i < L::Q; ++i) {
+        const int k = L::shell(i);
+        const T uc = T(L::cx(i)) * u[0] + T(L::cy(i)) * u[1] + T(L::cz(i)) * u[2];
+        const T X = uc * ics2 + T(0.5) * uc * uc * ics2 * ics2 - T(0.5) * uu * ics2;
+        const T w = weight<LAT, T>(k, cs2);
+        const T dev = w * rs * X + w * drs +
+                      T(p.rho0) * dcs2 *
+                          (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) + T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
+        stored_sum += double(pop_put<S, T>(p, dst, i, s, C::DEV ? dev : w * rs * (T(1) + X)));
+    }
+    // the rest population closes the sum to rho (as the collision does)
+    const double rest = (C::DEV ? rho_in[s] - p.rho0 : rho_in[s]) - stored_sum;
+    pop_put<S, double>(p, dst, 0, s, rest);
+}
+
+template <int LAT, typename T, typename U>
+__global__ void k_fields_out(DevSim p, int pair, double* rho_out, double* u_out)
+{
+    using L = Lat<LAT>;
+    const long long s = gtid();
+    if (s >= p.N) return;
+    const T rs = T(p.rho0) + cp<T>(p.rho)[s];
+    const U* jt = cp<U>(p.jt[pair][p.us[pair].cur]);
+    if (rho_out) rho_out[s] = double(rs);
+    if (u_out)
+#pragma unroll
+        for (int a = 0; a < L::D; ++a)
+            u_out[a * p.N + s] = double((cp<T>(p.j0p)[a * p.N + s] + T(jt[a * p.N + s])) / rs);
+}
+
+template <int LAT, int S>
+__global__ void k_pops_out(DevSim p, int src, double* out)
+{
+    using L = Lat<LAT>;
+    using C = Codec<S>;
+    const long long s = gtid();
+    if (s >= p.N) return;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+        out[(long long)i * p.N + s] = pop_raw<S, double>(p, src, i, s) + (C::DEV ? p.off[L::shell(i)] : 0.0);
+}
+
+template <int LAT, int S>
+__global__ void k_pops_in(DevSim p, const double* in, int dst)
+{
+    using L = Lat<LAT>;
+    using C = Codec<S>;
+    const long long s = gtid();
+    if (s >= p.N) return;
+#pragma unroll
+    for (int i = 0; i < L::Q; ++i)
+        pop_put<S, double>(p, dst, i, s, in[(long long)i * p.N + s] - (C::DEV ? p.off[L::shell(i)] : 0.0));
+}
+
+// FP64 sums of rho and sum_i n_i c_i: fixed grid, fixed tree, so the result is
+// independent of scheduling.  Each block writes its 4 partial sums.
+constexpr int RED_BLOCK = kRedBlock;
+constexpr int RED_GRID = kRedGrid;
+
+template <int LAT, int S>
+__global__ void k_red_partial(DevSim p, int src, double* part)
+{
+    using L = Lat<LAT>;
+    using C = Codec<S>;
+    __shared__ double sm[4][RED_BLOCK];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (long long s = blockIdx.x * (long long)RED_BLOCK + threadIdx.x; s < p.N; s += (long long)RED_GRID * RED_BLOCK) {
+#pragma unroll
+        for (int i = 0; i < L::Q; ++i) {
+            const double v = pop_raw<S, double>(p, src, i, s) + (C::DEV ? p.off[L::shell(i)] : 0.0);
+            acc[0] += v;
+            acc[1] += L::cx(i) * v;
+            acc[2] += L::cy(i) * v;
+            acc[3] += L::cz(i) * v;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sm[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int w = RED_BLOCK / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sm[c][threadIdx.x] += sm[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) part[blockIdx.x * 4 + threadIdx.x] = sm[threadIdx.x][0];
+}
+
+static __global__ void k_red_final(DevSim p, const double* part, int nparts, double* out)
+{
+    __shared__ double sm[4][RED_BLOCK];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < nparts; k += RED_BLOCK)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[c] += part[k * 4 + c];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) sm[c][threadIdx.x] = acc[c];
+    __syncthreads();
+    for (int w = RED_BLOCK / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) sm[c][threadIdx.x] += sm[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[threadIdx.x] = sm[threadIdx.x][0];
+}
+
+template <int LAT, typename U>
+__global__ void k_copy_jt(DevSim p)
+{
+    using L = Lat<LAT>;
+    const long long s = gtid();
+    if (s >= p.N) return;
+    const U* src = cp<U>(p.jt[0][p.us[0].cur]);
+    U* dst = mp<U>(p.jt[1][0]);
+#pragma unroll
+    for (int a = 0; a < L::D; ++a) dst[a * p.N + s] = src[a * p.N + s];
+}
+
+// ---------------------------------------------------------------------------
+// Kernel table of one combination
+// ---------------------------------------------------------------------------
+template <int LAT, typename T, int S, typename U>
+KernelTable make_table(bool read_pops)
+{
+    KernelTable t{};
+    t.moments = (const void*)k_moments<LAT, T, S, U>;
+    t.force = (const void*)k_force<LAT, T>;
+    t.us_begin = (const void*)k_us_begin;
+    t.sweep = (const void*)k_sweep<LAT, T, U>;
+    t.us_ctl = (const void*)k_us_ctl;
+    t.derivs = (const void*)k_derivs<LAT, T, U>;
+    t.collide = read_pops ? (const void*)k_collide<LAT, T, S, U, true> : (const void*)k_collide<LAT, T, S, U, false>;
+    t.init_eq = (const void*)k_init_eq<LAT, T, S>;
+    t.fields_out = (const void*)k_fields_out<LAT, T, U>;
+    t.pops_out = (const void*)k_pops_out<LAT, S>;
+    t.pops_in = (const void*)k_pops_in<LAT, S>;
+    t.red_partial = (const void*)k_red_partial<LAT, S>;
+    t.red_final = (const void*)k_red_final;
+    t.copy_jt = (const void*)k_copy_jt<LAT, U>;
+    t.block = 256;
+    using TL = Tile<Lat<LAT>::D>;
+    t.tile[0] = TL::TX;
+    t.tile[1] = TL::TY;
+    t.tile[2] = TL::ZB;
+    t.tile_threads = TL::THREADS;
+    constexpr int D = Lat<LAT>::D;
+    t.smem_sweep = size_t(TL::NZR) * (4 * (TL::TX + 8) * (TL::TY + 8) + (D == 3 ? 6 : 3) * (TL::TX + 4) * (TL::TY + 4)) * sizeof(U);
+    t.smem_derivs = size_t(TL::NZR) * 6 * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
+    t.smem_collide = size_t(TL::NZR) * (1 + AuxLayout<D>::NB + D) * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
+    cudaFuncSetAttribute(t.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_sweep));
+    cudaFuncSetAttribute(t.derivs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_derivs));
+    cudaFuncSetAttribute(t.collide, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_collide));
+    t.tsize = sizeof(T);
+    t.usize = sizeof(U);
+    t.ssize = sizeof(typename Codec<S>::type);
+    t.rsize = Codec<S>::SPLIT0 ? sizeof(float2) : 0;
+    t.exact = Codec<S>::EXACT;
+    return t;
+}
+
+}  // namespace lbm

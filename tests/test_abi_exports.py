@@ -1,0 +1,55 @@
+"""The C-ABI library loads and exports every entry point include/lbm.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1402_2920_gb300 as P
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1402_2920_gb300 import build
+
+    build.build()
+    return P.load_library()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    declared = _declared()
+    assert set(declared) == set(P.ENTRY_POINTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_host_only_entry_points(lib):
+    assert P.lbm_velocities(P.LBM_D2Q21).shape == (21, 3)
+    c = P.lbm_velocities(P.LBM_D3Q59)
+    assert c.shape == (59, 3) and (c.sum(axis=0) == 0).all()
+    assert P.lbm_error_string(P.LBM_E_WEIGHTS).startswith("c_s^2")
+    assert P.lbm_footprint_bytes(P.LBM_D3Q59, (256, 256, 256), P.LBM_STORE_F32) > 256 ** 3 * 2 * 59 * 4
+    assert P.lbm_footprint_bytes(P.LBM_D3Q59, (256, 256, 3), P.LBM_STORE_F32) == 0  # invalid dims
+
+
+def test_no_cpu_fallback_without_gpu(lib):
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present")
+    except ImportError:
+        pass
+    eos = P.make_eos(P.LBM_EOS_VDW, a=1.7, b=1.0 / 3.0, T=1.5)
+    with pytest.raises(P.LbmError) as e:
+        P.Sim(P.LBM_D2Q21, (16, 16), eos, P.make_params(kappa=0.05))
+    assert e.value.code == P.LBM_E_CUDA
