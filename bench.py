@@ -85,22 +85,27 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def _algorithmic_bytes(lattice, storage_bytes, read_pops):
-    """Bytes each kernel must move per site if every input and output is touched once (FP32 fields)."""
+def _algorithmic_bytes(lattice, storage_bytes, read_pops, chebyshev=True):
+    """Bytes each kernel must move per site if every input and output is touched once (FP32 fields).
+
+    The rest population of the deviation storages is a float pair (8 bytes) and the density
+    carries its float remainder rho_lo (4 bytes), both read once per step by the collision."""
     Q, d = (59, 3) if lattice == 1 else (21, 2)
     naux = 26 if lattice == 1 else 13
     f = 4
+    pops = (Q - 1) * storage_bytes + 8
     return {
-        # read the populations, write rho - rho0 and j0
-        "moments": Q * storage_bytes + (1 + d) * f,
-        # read rho - rho0 and j0, write f and j0'
-        "force": f + d * f + 2 * d * f,
-        # read rho - rho0, j0', j~, write j~new
-        "usolve_sweep": f + 3 * d * f,
-        # read rho - rho0, j0', j~, write A, B, C, the local Sigma and Xi'
+        # read the populations, write rho - rho0, rho_lo and j0
+        "moments": pops + (2 + d) * f,
+        # read rho - rho0, j0 and the warm-start j~; write f, j0' and the starting u
+        "force": f + 2 * d * f + 3 * d * f,
+        # read u, rho - rho0, j0'; write u (Chebyshev: read and write the update vector too)
+        "usolve_sweep": f + 3 * d * f + (2 * d * f if chebyshev else 0),
+        # read u, rho - rho0, j0'; write A, B, C, the local Sigma and Xi'
         "derivs": f + 2 * d * f + naux * f,
-        # read A, B, C, Sigma_local, Xi', rho - rho0, j0', j~, f; write (and for gamma != 0 read) the populations
-        "collide": naux * f + f + 3 * d * f + Q * storage_bytes * (2 if read_pops else 1),
+        # read A, B, C, Sigma_local, Xi', rho - rho0, rho_lo, u, j0', f; write j~ and the populations
+        # (gamma != 0 also reads them)
+        "collide": naux * f + 2 * f + 4 * d * f + pops * (2 if read_pops else 1),
     }
 
 
@@ -215,10 +220,10 @@ def run_native(args):
     stream = torch.cuda.current_stream()
 
     def make_sim(st):
-        # u-solve over-relaxed with omega = 2/(2 - g) over the workload's density range
+        # u-solve sweeps Chebyshev-accelerated for the spectrum bound g over the workload's density range
         prm = P.make_params(gamma=case.gamma, kappa=case.kappa, rho0=case.rho0, storage=st,
                             rho_check_min=0.98 * case.eos.rho_g, rho_check_max=1.02 * case.eos.rho_l,
-                            usolve_omega=0.0)
+                            usolve_omega=0.0, usolve_chebyshev=1)
         return P.Sim(case.lattice, case.dims, P.make_eos(P.LBM_EOS_VDW, a=a, b=b, T=T), prm, stream.cuda_stream)
 
     def timed(sim, K, Wm):
@@ -321,7 +326,7 @@ def run_native(args):
                                        "kappa=%.5f, gamma=0" % (case.Tr, case.kappa),
                            "storage": {"f32": "FP32 populations", "f32dev": "FP32 deviations n_i - w_i(rho0) rho0",
                                        "f16dev": "FP16 deviations", "bf16dev": "BF16 deviations"}[args.storage],
-                           "usolve": "FP32 Jacobi, omega = 2/(2 - g), |dj~| <= 5e-9",
+                           "usolve": "FP32 sweeps, Chebyshev-accelerated for the spectrum [0, g], |dj~| <= 5e-9",
                            "parallelism": "replicas x%d" % ws, "l2": "inputs (populations 7.9 GB) larger than L2",
                            "sites": N},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

@@ -98,6 +98,11 @@ typedef struct {
                               with spectral radius below 1).  0 selects 2/(2 - g), g the largest
                               frozen-coefficient eigenvalue over [rho_check_min, rho_check_max]
                               (1 when no range is given).                                   */
+    int usolve_chebyshev;  /* 1: Chebyshev acceleration of the sweeps for the spectrum [0, g] of
+                              the iteration (g as for usolve_omega; needs the density range),
+                              about half the sweeps of the best plain relaxation; it falls
+                              back to plain sweeps within a solve if the residual grows.  The
+                              fixed point, and so the result up to the tolerance, is unchanged */
 } lbm_params;
 
 typedef struct {

@@ -127,32 +127,44 @@ void weight_window(double& lo, double& hi)
     hi = a;
 }
 
-// Largest eigenvalue of the u-solve iteration for frozen coefficients at density rho:
-// (|s|^2 / 12) max(3 c_s^2 - p', c_s^2), |s|^2 <= d max_k s(k)^2 with s(k) the symbol
-// (4/3) sin k - (1/6) sin 2k of the Sec. IV.B first derivative.
-double frozen_gain(const lbm_eos& e, double rho, int d)
+// The parameters and derived constants of the kernels in arithmetic T (see Phys).
+template <typename T>
+void fill_phys(Phys<T>& q, const DevSim& dv, const lbm_eos& e)
 {
-    double smax = 0.0;
-    for (int k = 0; k <= 20000; ++k) {
-        const double x = M_PI * k / 20000.0;
-        smax = std::fmax(smax, std::fabs(4.0 / 3.0 * std::sin(x) - std::sin(2.0 * x) / 6.0));
+    const double g = dv.gamma, c0 = dv.cs0;
+    q.rho0 = T(dv.rho0);
+    q.cs0 = T(c0);
+    q.gamma = T(g);
+    q.kappa = T(dv.kappa);
+    q.omega = T(dv.omega);
+    q.a = T(e.a);
+    q.b = T(e.b);
+    q.Teos = T(e.T);
+    q.bT = T(e.b * e.T);
+    q.g0 = T(1.0 - e.b * dv.rho0);
+    const double D = e.kind == LBM_EOS_PSI_SINE ? e.rho2 - e.rho1 : 1.0;
+    q.rho1 = T(e.rho1);
+    q.rho3 = T(2.0 * e.rho2 - e.rho1);
+    q.cs2_1 = T(e.cs2_rho1);
+    q.A = T(e.A);
+    q.pi_D = T(M_PI / D);
+    q.A_pi_D = T(e.A * M_PI / D);
+    q.AD_pi = T(e.A * D / M_PI);
+    q.ph0 = T(M_PI * (dv.rho0 - e.rho1) / D);
+    q.cs2_lo = T(dv.cs2_lo);
+    q.cs2_hi = T(dv.cs2_hi);
+    for (int k = 0; k < 8; ++k) {
+        q.w0[k] = T(dv.w0[k]);
+        q.off[k] = T(dv.off[k]);
     }
-    double ev[4];
-    host_eos(e, rho, ev);
-    const double cs2 = ev[0] / rho;
-    return d * smax * smax / 12.0 * std::fmax(3.0 * cs2 - ev[1], cs2);
-}
-
-// omega = 2 / (2 - g) for the spectrum [0, g] of the iteration, g from the frozen
-// coefficients over the create-time density range (with 2 % margin); 1 without a range.
-double auto_omega(const lbm_eos& e, const lbm_params& prm, int d)
-{
-    if (!(prm.rho_check_max > prm.rho_check_min && prm.rho_check_min > 0.0)) return 1.0;
-    double g = 0.0;
-    for (int k = 0; k <= 400; ++k)
-        g = std::fmax(g, frozen_gain(e, prm.rho_check_min + (prm.rho_check_max - prm.rho_check_min) * k / 400.0, d));
-    g = std::fmin(0.95, 1.02 * g);
-    return 2.0 / (2.0 - g);
+    q.k1 = T(-0.25 * (g + 1.0) * (g + 1.0) / (g - 1.0));
+    q.k2 = T((1.0 / 6.0) * (g * g + 4.0 * g + 1.0) / (g - 1.0));
+    q.k3 = T((1.0 / 3.0) * (g * g + 4.0 * g + 1.0) / (g + 1.0));
+    q.cf_int = T(0.5 * (1.0 + g) / c0);
+    q.cf_jt = T((g - 1.0) / c0);
+    q.cf_h2 = T(0.5 / (c0 * c0));
+    q.cf_h3 = T(1.0 / (6.0 * c0 * c0 * c0));
+    q.cj = T((1.0 - g) * c0);
 }
 
 size_t bytes_per_site(int lattice, int storage, size_t* ssize_out = nullptr)
@@ -211,7 +223,7 @@ int add_step(lbm_sim* s, cudaGraph_t g, cudaGraphNode_t dep, int src, cudaGraphN
         LBM_CK(add_kernel(g, &n1, s->kt.moments, dim3(G), B, a, d0, nd0));
     }
     {
-        void* a[] = {&dv};
+        void* a[] = {&dv, &pair};
         LBM_CK(add_kernel(g, &n2, s->kt.force, dim3(G), B, a, &n1, 1));
     }
     {
@@ -319,9 +331,14 @@ int reset_usolve(lbm_sim* s)
     UsolveState z[2];
     std::memset(z, 0, sizeof(z));
     LBM_CK(cudaMemcpyAsync(s->dev.us, z, sizeof(z), cudaMemcpyHostToDevice, s->stream));
+    std::vector<unsigned> rg(4 * kRangeSlots);
+    for (int k = 0; k < 4 * kRangeSlots; ++k) rg[k] = ((k / kRangeSlots) % 2 == 0) ? 0x7f7fffffu : 0u;
+    LBM_CK(cudaMemcpyAsync(s->dev.range, rg.data(), rg.size() * sizeof(unsigned), cudaMemcpyHostToDevice, s->stream));
+    LBM_CK(cudaStreamSynchronize(s->stream));  // rg lives on this stack
     const size_t jbytes = 3 * size_t(s->dev.N) * s->kt.usize;
     for (int pr = 0; pr < 2; ++pr)
-        for (int b = 0; b < 2; ++b) LBM_CK(cudaMemsetAsync(s->dev.jt[pr][b], 0, jbytes, s->stream));
+        for (int b = 0; b < 2; ++b) LBM_CK(cudaMemsetAsync(s->dev.uit[pr][b], 0, jbytes, s->stream));
+    LBM_CK(cudaMemsetAsync(s->dev.jt_warm, 0, jbytes, s->stream));
     const int zi = 0;
     LBM_CK(cudaMemcpyAsync(s->dev.status, &zi, sizeof(int), cudaMemcpyHostToDevice, s->stream));
     return LBM_OK;
@@ -340,11 +357,8 @@ int run_fields(lbm_sim* s)
     DevSim& dv = s->dev;
     const int B = s->kt.block, G = nblocks(dv.N, B);
     const int pair = 1;
-    LBM_CK(launch(s, s->kt.copy_jt, G, B, dv));
-    const int zero = 0;
-    LBM_CK(cudaMemcpyAsync(&dv.us[1].cur, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream));
     LBM_CK(launch(s, s->kt.moments, G, B, dv, s->cur, pair));
-    LBM_CK(launch(s, s->kt.force, G, B, dv));
+    LBM_CK(launch(s, s->kt.force, G, B, dv, pair));
     LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
     cudaGraphConditionalHandle h{};
     const int no = 0;
@@ -509,9 +523,20 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
         dv.rtol = 0.0;
     }
     if (!(params->usolve_omega >= 0.0 && params->usolve_omega < 2.0)) { lbm_destroy(s); return LBM_E_INVALID_ARG; }
-    dv.omega = params->usolve_omega > 0.0 ? params->usolve_omega : auto_omega(*eos, *params, d);
+    dv.omega = params->usolve_omega;  // 0: 2/(2 - g) per solve
     dv.maxit = params->usolve_max_iter > 0 ? params->usolve_max_iter : 500;
     dv.warm = params->usolve_warm_start ? 1 : 0;
+    {
+        double smax = 0.0;  // max_k |(4/3) sin k - (1/6) sin 2k|, the Sec. IV.B symbol
+        for (int k = 0; k <= 20000; ++k) {
+            const double x = M_PI * k / 20000.0;
+            smax = std::fmax(smax, std::fabs(4.0 / 3.0 * std::sin(x) - std::sin(2.0 * x) / 6.0));
+        }
+        dv.s2max = smax * smax;
+        dv.cheb = params->usolve_chebyshev ? 1 : 0;  // the bound of each solve comes from its density range
+    }
+    fill_phys<float>(dv.pf, dv, *eos);
+    fill_phys<double>(dv.pd, dv, *eos);
 
     const size_t N = size_t(dv.N);
     const size_t T = s->kt.tsize, U = s->kt.usize, SS = s->kt.ssize;
@@ -527,12 +552,20 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
     rc = rc ? rc : dev_alloc(s, &dv.j0p, 3 * N * T);
     rc = rc ? rc : dev_alloc(s, &dv.f, 3 * N * T);
     for (int pr = 0; pr < 2; ++pr)
-        for (int b = 0; b < 2; ++b) rc = rc ? rc : dev_alloc(s, &dv.jt[pr][b], 3 * N * U);
+        for (int b = 0; b < 2; ++b) rc = rc ? rc : dev_alloc(s, &dv.uit[pr][b], 3 * N * U);
+    rc = rc ? rc : dev_alloc(s, &dv.jt_warm, 3 * N * U);
     rc = rc ? rc : dev_alloc(s, &dv.q, 6 * N * U);
+    if (dv.cheb) {
+        rc = rc ? rc : dev_alloc(s, &dv.dvec[0], 3 * N * U);
+        rc = rc ? rc : dev_alloc(s, &dv.dvec[1], 3 * N * U);
+    }
     rc = rc ? rc : dev_alloc(s, &dv.aux, size_t(MAX_AUX) * N * T);
     void* usp = nullptr;
     rc = rc ? rc : dev_alloc(s, &usp, 2 * sizeof(UsolveState));
     dv.us = static_cast<UsolveState*>(usp);
+    void* rgp = nullptr;
+    rc = rc ? rc : dev_alloc(s, &rgp, 4 * kRangeSlots * sizeof(unsigned));
+    dv.range = static_cast<unsigned*>(rgp);
     void* stp = nullptr;
     rc = rc ? rc : dev_alloc(s, &stp, 256);
     dv.status = static_cast<int*>(stp);
@@ -589,6 +622,12 @@ int lbm_init(lbm_sim* s, const double* rho, const double* u, int on_device)
 
 namespace {
 
+bool trace_mode()
+{
+    const char* v = std::getenv("LBM_TRACE");
+    return v && v[0] == '1';
+}
+
 // One step with every kernel launched on its own and the u-solve loop driven
 // from the host (the same kernels and order as the graph).
 int step_direct(lbm_sim* s)
@@ -598,15 +637,18 @@ int step_direct(lbm_sim* s)
     const int pair = 0, no = 0, src = s->cur;
     cudaGraphConditionalHandle h{};
     LBM_CK(launch(s, s->kt.moments, G, B, dv, src, pair));
-    LBM_CK(launch(s, s->kt.force, G, B, dv));
+    LBM_CK(launch(s, s->kt.force, G, B, dv, pair));
     LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
     for (int it = 0; it < dv.maxit + 1; ++it) {
         LBM_CK(launch_tiled(s, s->kt.sweep, s->kt.smem_sweep, dv, pair));
         LBM_CK(launch(s, s->kt.us_ctl, 1, 1, dv, pair, h, no));
-        int running = 0;
-        LBM_CK(cudaMemcpyAsync(&running, &dv.us[0].running, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+        UsolveState u;
+        LBM_CK(cudaMemcpyAsync(&u, &dv.us[0], sizeof(u), cudaMemcpyDeviceToHost, s->stream));
         LBM_CK(cudaStreamSynchronize(s->stream));
-        if (!running) break;
+        if (trace_mode())  // the residual history of every u-solve, for tuning the solver
+            std::fprintf(stderr, "lbm usolve step %lld sweep %d resid %.3e mode %d next c1 %.4f c2 %.4f\n",
+                         (long long)s->steps, u.iter, u.running ? u.resid_min : u.resid_last, u.mode, u.c1, u.c2);
+        if (!u.running) break;
     }
     LBM_CK(launch_tiled(s, s->kt.derivs, s->kt.smem_derivs, dv));
     LBM_CK(launch_tiled(s, s->kt.collide, s->kt.smem_collide, dv, src));
@@ -632,8 +674,8 @@ int lbm_step(lbm_sim* s, int64_t nsteps)
         for (int64_t k = 0; k < nsteps; ++k) {
             const int rc = step_direct(s);
             if (rc) return rc;
+            s->steps += 1;
         }
-        s->steps += nsteps;
         return LBM_OK;
     }
     int64_t n = nsteps;
@@ -761,13 +803,18 @@ int lbm_profile(lbm_sim* s, int reps, double* ms_out, int n)
     DevSim& dv = s->dev;
     const int B = s->kt.block, G = nblocks(dv.N, B);
     const int src = s->cur, pair = 1;
+    // the collision kernel rewrites the warm-start j~: keep the run's copy aside
+    const size_t jbytes = 3 * size_t(dv.N) * s->kt.usize;
+    void* keep = nullptr;
+    LBM_CK(cudaMallocAsync(&keep, jbytes, s->stream));
+    LBM_CK(cudaMemcpyAsync(keep, dv.jt_warm, jbytes, cudaMemcpyDeviceToDevice, s->stream));
     cudaEvent_t e0, e1;
     LBM_CK(cudaEventCreate(&e0));
     LBM_CK(cudaEventCreate(&e1));
-    // scratch u-solve pair starts from the run's j~; the collision writes the spare buffer
-    LBM_CK(launch(s, s->kt.copy_jt, G, B, dv));
-    const int zero = 0;
-    LBM_CK(cudaMemcpyAsync(&dv.us[1].cur, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream));
+    // the scratch u-solve pair; the collision writes the spare population buffer
+    LBM_CK(launch(s, s->kt.moments, G, B, dv, src, pair));
+    LBM_CK(launch(s, s->kt.force, G, B, dv, pair));
+    LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
     int rc = LBM_OK;
     for (int k = 0; k < 5 && rc == LBM_OK; ++k) {
         for (int r = 0; r <= reps && rc == LBM_OK; ++r) {
@@ -775,7 +822,7 @@ int lbm_profile(lbm_sim* s, int reps, double* ms_out, int n)
             cudaError_t e = cudaSuccess;
             switch (k) {
             case 0: e = launch(s, s->kt.moments, G, B, dv, src, pair); break;
-            case 1: e = launch(s, s->kt.force, G, B, dv); break;
+            case 1: e = launch(s, s->kt.force, G, B, dv, pair); break;
             case 2: e = launch_tiled(s, s->kt.sweep, s->kt.smem_sweep, dv, pair); break;
             case 3: e = launch_tiled(s, s->kt.derivs, s->kt.smem_derivs, dv); break;
             case 4: e = launch_tiled(s, s->kt.collide, s->kt.smem_collide, dv, src); break;
@@ -791,10 +838,12 @@ int lbm_profile(lbm_sim* s, int reps, double* ms_out, int n)
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     (void)cudaGetLastError();
-    // the scratch residual accumulators were left mid-loop: clear them
+    // the scratch residual accumulators were left mid-loop: clear them; restore the warm start
     UsolveState u1{};
     if (rc == LBM_OK && cudaMemcpyAsync(&dv.us[1], &u1, sizeof(u1), cudaMemcpyHostToDevice, s->stream) != cudaSuccess)
         rc = LBM_E_CUDA;
+    if (cudaMemcpyAsync(dv.jt_warm, keep, jbytes, cudaMemcpyDeviceToDevice, s->stream) != cudaSuccess) rc = LBM_E_CUDA;
+    if (cudaFreeAsync(keep, s->stream) != cudaSuccess) rc = LBM_E_CUDA;
     if (rc == LBM_OK && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = LBM_E_CUDA;
     return rc;
 }
@@ -823,7 +872,7 @@ int lbm_save(lbm_sim* s, const char* path)
     LBM_CK(cudaMemcpy(us, s->dev.us, sizeof(us), cudaMemcpyDeviceToHost));
     LBM_CK(cudaMemcpy(buf.data(), s->dev.pop[s->cur], pbytes, cudaMemcpyDeviceToHost));
     if (zbytes) LBM_CK(cudaMemcpy(buf.data() + pbytes, s->dev.pop0[s->cur], zbytes, cudaMemcpyDeviceToHost));
-    LBM_CK(cudaMemcpy(buf.data() + pbytes + zbytes, s->dev.jt[0][us[0].cur], jbytes, cudaMemcpyDeviceToHost));
+    LBM_CK(cudaMemcpy(buf.data() + pbytes + zbytes, s->dev.jt_warm, jbytes, cudaMemcpyDeviceToHost));
     CkptHeader h{};
     std::memcpy(h.magic, "LBM2PH01", 8);
     h.lattice = s->lattice;
@@ -875,7 +924,7 @@ int lbm_load(lbm_sim* s, const char* path)
     u0.jmax_bits = 0;
     LBM_CK(cudaMemcpy(s->dev.pop[0], buf.data(), pbytes, cudaMemcpyHostToDevice));
     if (zbytes) LBM_CK(cudaMemcpy(s->dev.pop0[0], buf.data() + pbytes, zbytes, cudaMemcpyHostToDevice));
-    LBM_CK(cudaMemcpy(s->dev.jt[0][0], buf.data() + pbytes + zbytes, jbytes, cudaMemcpyHostToDevice));
+    LBM_CK(cudaMemcpy(s->dev.jt_warm, buf.data() + pbytes + zbytes, jbytes, cudaMemcpyHostToDevice));
     LBM_CK(cudaMemcpy(&s->dev.us[0], &u0, sizeof(u0), cudaMemcpyHostToDevice));
     s->steps = h.steps;
     return LBM_OK;

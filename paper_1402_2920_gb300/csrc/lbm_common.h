@@ -25,7 +25,18 @@ struct UsolveState {
     int converged;                  // 1 once the last solve met its tolerance
     int running;                    // 1 from k_us_begin until the control kernel stops the loop
     long long sweeps_total;         // sweeps since the last reset
+    // the update of the next sweep: d = c1 d_prev + c2 (J(j~) - j~), j~ += d
+    double c1, c2;
+    double cheb_rho;                // Chebyshev recurrence variable
+    double cheb_sigma, cheb_delta;  // this solve's spectrum [1 - g, 1] of I - A (theta = 1 - g/2)
+    double gain;                    // this solve's bound g, from the density range of the state
+    double resid_min;               // smallest residual of the solve so far (divergence guard)
+    int mode;                       // 1: Chebyshev acceleration, 0: plain relaxation
+    int pad[2];
 };
+
+// slots of the density-range reduction (spread so that block atomics do not contend)
+constexpr int kRangeSlots = 64;
 
 // Launch shape of the FP64 conservation sums (fixed, so the reduction order is fixed).
 constexpr int kRedBlock = 256;
@@ -33,6 +44,19 @@ constexpr int kRedGrid = 1024;
 
 // Error bits recorded by kernels (read back by lbm_sync and friends).
 enum StatusBits { STB_WEIGHTS = 1, STB_NONFINITE_RHO = 2, STB_USOLVE_CAP = 4, STB_USOLVE_NAN = 8 };
+
+// Physical parameters and derived constants in the kernel arithmetic T, filled on the
+// host so that device code neither converts from double nor divides per site.
+template <typename T>
+struct Phys {
+    T rho0, cs0, gamma, kappa, omega;
+    T a, b, Teos, bT, g0;                 // van der Waals; bT = b T, g0 = 1 - b rho0
+    T rho1, rho3, cs2_1, A, pi_D, A_pi_D, AD_pi, ph0;  // psi-sine: pi/D, A pi/D, A D/pi, phase at rho0
+    T cs2_lo, cs2_hi;                     // positive-weight window
+    T w0[8], off[8];                      // w_k(c_s^2(rho0)) and w_k rho0 per shell
+    T k1, k2, k3;                         // prefactors of Sigma (two) and Xi' (Sec. VIII, S11)
+    T cf_int, cf_jt, cf_h2, cf_h3, cj;    // (1+g)/(2 cs0), (g-1)/cs0, 1/(2 cs0^2), 1/(6 cs0^3), (1-g) cs0
+};
 
 // Everything a kernel needs, passed by value (lives in the kernel parameter space).
 struct DevSim {
@@ -47,10 +71,13 @@ struct DevSim {
     void* rho;            // T [N]: rho - rho0 (exact differences; rho0 + it recovers rho)
     void* j0p;            // T [3][N]: j0 after S1, j0' = j0 + f/2 after S2
     void* f;              // T [3][N]: interface force
-    void* jt[2][2];       // U [3][N]: j~ ping-pong buffers of pair 0 (the run) and pair 1 (lbm_fields)
+    void* uit[2][2];      // U [3][N]: u iterates of the u-solve, ping-pong, for pair 0 (the run)
+                          // and pair 1 (lbm_fields); u = (j0' + j~)/rho (S3)
+    void* jt_warm;        // U [3][N]: j~ = rho u - j0' of the last step, the warm start (Sec. IX)
     void* q;              // U [6][N]: symmetric q_ab of the u-solve (S4)
     void* aux;            // T [26][N]: A, B_ab, C_a, the local part of Sigma_ab, Xi'_abc
     UsolveState* us;      // [2]: pair 0 and pair 1
+    unsigned* range;      // [2][2][kRangeSlots]: float bits of min and max density per pair
     int* status;          // error bits
     double* red;          // reduction scratch
     // physics
@@ -62,14 +89,20 @@ struct DevSim {
     double rho1, rho2, A, cs2_1;
     double cs2_lo, cs2_hi;           // positive-weight window (Sec. III)
     double tol, rtol;
-    double omega;                    // relaxation of the u-solve sweep (1 = the plain iteration)
+    double omega;                    // relaxation of the u-solve sweep (1 = the plain iteration);
+                                     // 0: 2/(2 - g) with g the bound of each solve
+    int cheb;                        // Chebyshev acceleration of the sweeps
+    double s2max;                    // max over k of |s(k)|^2 of the first-derivative symbol (1D)
+    void* dvec[2];                   // U [3][N]: previous update of the u-solve, pair 0 and 1
     int maxit, warm;
+    Phys<float> pf;                  // the same parameters for FP32 arithmetic
+    Phys<double> pd;                 // and for FP64 arithmetic
 };
 
 // Kernels of one (lattice, arithmetic, storage, u-solve arithmetic) combination.
 struct KernelTable {
     const void* moments;      // (DevSim, int src, int pair)
-    const void* force;        // (DevSim)
+    const void* force;        // (DevSim, int pair): also the u-solve's starting u
     const void* us_begin;     // (DevSim, int pair)
     const void* sweep;        // (DevSim, int pair): one tiled u-solve sweep
     const void* us_ctl;       // (DevSim, int pair, cudaGraphConditionalHandle, int use_cond)
@@ -81,7 +114,6 @@ struct KernelTable {
     const void* pops_in;      // (DevSim, const double* in, int dst)
     const void* red_partial;  // (DevSim, int src, double* partials)
     const void* red_final;    // (DevSim, const double* partials, int nparts, double* out)
-    const void* copy_jt;      // (DevSim) copy pair-0 current j~ into pair-1 buffer 0
     int block;                // threads per block of the per-site kernels
     int tile[3];              // TX, TY, ZB of the tiled kernels
     int tile_threads;

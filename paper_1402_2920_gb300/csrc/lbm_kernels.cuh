@@ -115,6 +115,13 @@ struct Codec<ST_F64> {
     __device__ static T rounded(T v) { return T(double(v)); }
 };
 
+template <typename T>
+__device__ __forceinline__ const Phys<T>& phys(const DevSim& p);
+template <>
+__device__ __forceinline__ const Phys<float>& phys<float>(const DevSim& p) { return p.pf; }
+template <>
+__device__ __forceinline__ const Phys<double>& phys<double>(const DevSim& p) { return p.pd; }
+
 // ---------------------------------------------------------------------------
 // Equation of state (App. B; S1).  P = p, DP = dp/drho, PM = p - rho dp/drho,
 // RPP = rho d2p/drho2.
@@ -122,24 +129,22 @@ struct Codec<ST_F64> {
 template <typename T>
 __device__ __forceinline__ void eos_full(const DevSim& p, T rho, T& P, T& DP, T& PM, T& RPP)
 {
+    const Phys<T>& q = phys<T>(p);
     if (p.eos_kind == 0) {
-        const T g = T(1) - T(p.b) * rho;
-        const T ig = T(1) / g;
-        P = rho * T(p.T) * ig - T(p.a) * rho * rho;
-        DP = T(p.T) * ig * ig - T(2) * T(p.a) * rho;
-        RPP = rho * (T(2) * T(p.b) * T(p.T) * ig * ig * ig - T(2) * T(p.a));
+        const T ig = T(1) / (T(1) - q.b * rho);
+        P = rho * q.Teos * ig - q.a * rho * rho;
+        DP = q.Teos * ig * ig - T(2) * q.a * rho;
+        RPP = rho * (T(2) * q.bT * ig * ig * ig - T(2) * q.a);
     } else {
-        const T D = T(p.rho2) - T(p.rho1);
-        const T rho3 = T(2) * T(p.rho2) - T(p.rho1);
         T psi = T(0), dpsi = T(0), integ = T(0);
-        if (rho > T(p.rho1) && rho < rho3) {
-            const T ph = T(3.14159265358979323846) * (rho - T(p.rho1)) / D;
+        if (rho > q.rho1 && rho < q.rho3) {
+            const T ph = q.pi_D * (rho - q.rho1);
             const T sn = sin(ph), cn = cos(ph);
-            psi = T(p.A) * sn;
-            dpsi = T(p.A) * T(3.14159265358979323846) / D * cn;
-            integ = T(p.A) * D / T(3.14159265358979323846) * (T(1) - cn);
+            psi = q.A * sn;
+            dpsi = q.A_pi_D * cn;
+            integ = q.AD_pi * (T(1) - cn);
         }
-        const T cs2 = T(p.cs2_1) * exp(integ);
+        const T cs2 = q.cs2_1 * exp(integ);
         P = rho * cs2;
         DP = cs2 * (T(1) + rho * psi);
         RPP = rho * (cs2 * psi * (T(1) + rho * psi) + cs2 * (psi + rho * dpsi));
@@ -150,6 +155,8 @@ __device__ __forceinline__ void eos_full(const DevSim& p, T rho, T& P, T& DP, T&
 template <typename T>
 __device__ __forceinline__ T eos_p(const DevSim& p, T rho)
 {
+    const Phys<T>& q = phys<T>(p);
+    if (p.eos_kind == 0) return rho * q.Teos / (T(1) - q.b * rho) - q.a * rho * rho;
     T P, DP, PM, RPP;
     eos_full(p, rho, P, DP, PM, RPP);
     return P;
@@ -160,24 +167,23 @@ __device__ __forceinline__ T eos_p(const DevSim& p, T rho)
 template <typename T>
 __device__ __forceinline__ void cs2_delta(const DevSim& p, T drho, T& s, T& ds)
 {
-    const T rho = T(p.rho0) + drho;
+    const Phys<T>& q = phys<T>(p);
+    const T rho = q.rho0 + drho;
     if (p.eos_kind == 0) {
         // s = T/(1 - b rho) - a rho  =>  s - s0 = drho (T b / ((1 - b rho)(1 - b rho0)) - a)
-        const T g = T(1) - T(p.b) * rho, g0 = T(1.0 - p.b * p.rho0);
-        s = T(p.T) / g - T(p.a) * rho;
-        ds = drho * (T(p.T) * T(p.b) / (g * g0) - T(p.a));
+        const T g = T(1) - q.b * rho;
+        s = q.Teos / g - q.a * rho;
+        ds = drho * (q.bT / (g * q.g0) - q.a);
     } else {
         // s = cs2(rho1) exp(I), I = (A D / pi)(1 - cos phi), phi = pi (rho - rho1)/D clamped to [0, 2 pi]
-        const T D = T(p.rho2) - T(p.rho1);
         const T PI = T(3.14159265358979323846);
-        const T ph_raw = PI * (rho - T(p.rho1)) / D, ph0_raw = T(M_PI * (p.rho0 - p.rho1) / (p.rho2 - p.rho1));
-        const T ph = fmin(fmax(ph_raw, T(0)), T(2) * PI), ph0 = fmin(fmax(ph0_raw, T(0)), T(2) * PI);
-        const bool inside = ph == ph_raw && ph0 == ph0_raw;
-        const T dph = inside ? PI * drho / D : ph - ph0;
-        const T dI = T(p.A) * D / PI * T(2) * sin(T(0.5) * (ph + ph0)) * sin(T(0.5) * dph);
-        const T s0 = T(p.cs0);
-        ds = s0 * expm1(dI);
-        s = s0 + ds;
+        const T ph_raw = q.pi_D * (rho - q.rho1);
+        const T ph = fmin(fmax(ph_raw, T(0)), T(2) * PI), ph0 = fmin(fmax(q.ph0, T(0)), T(2) * PI);
+        const bool inside = ph == ph_raw && ph0 == q.ph0;
+        const T dph = inside ? q.pi_D * drho : ph - ph0;
+        const T dI = q.AD_pi * T(2) * sin(T(0.5) * (ph + ph0)) * sin(T(0.5) * dph);
+        ds = q.cs0 * expm1(dI);
+        s = q.cs0 + ds;
     }
 }
 
@@ -346,8 +352,9 @@ __global__ void k_moments(DevSim p, int src, int pair)
 {
     using L = Lat<LAT>;
     using C = Codec<S>;
-    const long long s = gtid();
-    if (s >= p.N) return;
+    const long long s0 = gtid();
+    const long long s = s0 < p.N ? s0 : p.N - 1;  // the tail recomputes the last site (same values)
+    const bool own = s0 < p.N;
     T sum = T(0), j[3] = {T(0), T(0), T(0)};
     float hi = 0.f, lo = 0.f;
     if (C::EXACT) {
@@ -370,35 +377,52 @@ __global__ void k_moments(DevSim p, int src, int pair)
     if (C::EXACT) {
         if (!C::DEV) {
             float e;
-            two_sum(hi, -float(p.rho0), hi, e);
+            two_sum(hi, -p.pf.rho0, hi, e);
             lo = __fadd_rn(lo, e);
         }
         float e;
         two_sum(hi, lo, hi, e);  // renormalise: hi = the float nearest to the pair
         drho = T(hi);
-        mp<float>(p.rho_lo)[s] = e;  // the part float drops
+        if (own) mp<float>(p.rho_lo)[s] = e;  // the part float drops
     } else {
-        drho = C::DEV ? sum : sum - T(p.rho0);
+        drho = C::DEV ? sum : sum - phys<T>(p).rho0;
     }
-    const T r = T(p.rho0) + drho;
-    mp<T>(p.rho)[s] = drho;
+    const T r = phys<T>(p).rho0 + drho;
+    if (own) mp<T>(p.rho)[s] = drho;
+    if (own)
 #pragma unroll
-    for (int a = 0; a < L::D; ++a) mp<T>(p.j0p)[a * p.N + s] = j[a];
-    if (!p.warm) {
-        U* jt = mp<U>(p.jt[pair][p.us[pair].cur]);
+        for (int a = 0; a < L::D; ++a) mp<T>(p.j0p)[a * p.N + s] = j[a];
+    {  // density range of the state (bounds the spectrum of the u-solve iteration): one atomic per block
+        __shared__ float slo[32], shi[32];
+        float lo = float(r), hi = float(r);
 #pragma unroll
-        for (int a = 0; a < L::D; ++a) jt[a * p.N + s] = U(0);
+        for (int o = 16; o > 0; o >>= 1) {
+            lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+            hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) { slo[warp] = lo; shi[warp] = hi; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int w = 1; w < int(blockDim.x >> 5); ++w) { lo = fminf(lo, slo[w]); hi = fmaxf(hi, shi[w]); }
+            if (lo > 0.f) {
+                unsigned* rg = p.range + pair * 2 * kRangeSlots;
+                const int slot = blockIdx.x % kRangeSlots;
+                atomicMin(rg + slot, __float_as_uint(lo));
+                atomicMax(rg + kRangeSlots + slot, __float_as_uint(hi));
+            }
+        }
     }
     const T cs2 = eos_p(p, r) / r;
     if (!isfinite(r)) atomicOr(p.status, STB_NONFINITE_RHO);
-    else if (!(cs2 > T(p.cs2_lo) && cs2 < T(p.cs2_hi))) atomicOr(p.status, STB_WEIGHTS);
+    else if (!(cs2 > phys<T>(p).cs2_lo && cs2 < phys<T>(p).cs2_hi)) atomicOr(p.status, STB_WEIGHTS);
 }
 
 // ---------------------------------------------------------------------------
 // S2: interface force (Sec. VI with the third-derivative stencil of Sec. IV.E)
 // ---------------------------------------------------------------------------
-template <int LAT, typename T>
-__global__ void k_force(DevSim p)
+template <int LAT, typename T, typename U>
+__global__ void k_force(DevSim p, int pair)
 {
     using L = Lat<LAT>;
     const long long s = gtid();
@@ -423,26 +447,71 @@ __global__ void k_force(DevSim p)
         }
         // sum_i tau_i d_ia rho(r + d_i): the (2 0) shell has d_a = +-2
         const T lap3 = T(L::T3_AX) * ax + T(L::T3_DIAG) * diag + T(2.0 * L::T3_TWO) * two;
-        f[a] = T(p.kappa) * (T(p.rho0) + drho[s]) * lap3;
+        f[a] = phys<T>(p).kappa * (phys<T>(p).rho0 + drho[s]) * lap3;
     }
+    // S2: j0' = j0 + (h/2) f; S3 for the start of the u-solve: u = (j0' + j~)/rho with j~ of the
+    // previous step (warm start, Sec. IX item 3) or j~ = 0 (S1)
+    const U rho = phys<U>(p).rho0 + U(drho[s]);
+    const U* jw = cp<U>(p.jt_warm);
+    U* u0 = mp<U>(p.uit[pair][p.us[pair].cur]);
 #pragma unroll
     for (int a = 0; a < L::D; ++a) {
         mp<T>(p.f)[a * p.N + s] = f[a];
-        mp<T>(p.j0p)[a * p.N + s] += T(0.5) * f[a];
+        const T j = mp<T>(p.j0p)[a * p.N + s] + T(0.5) * f[a];
+        mp<T>(p.j0p)[a * p.N + s] = j;
+        u0[a * p.N + s] = (U(j) + (p.warm ? jw[a * p.N + s] : U(0))) / rho;
     }
 }
 
 // ---------------------------------------------------------------------------
 // S3-S7: the implicit u-solve (Sec. IX)
 // ---------------------------------------------------------------------------
+// Frozen-coefficient largest eigenvalue of the iteration at density rho:
+// (d s2max / 12) max(3 c_s^2 - p', c_s^2), s2max = max_k |s(k)|^2 of the Sec. IV.B symbol.
+static __device__ double frozen_gain(const DevSim& p, double rho)
+{
+    double P, DP, PM, RPP;
+    eos_full<double>(p, rho, P, DP, PM, RPP);
+    const double cs2 = P / rho;
+    return p.d * p.s2max / 12.0 * fmax(3.0 * cs2 - DP, cs2);
+}
+
 static __global__ void k_us_begin(DevSim p, int pair)
 {
     UsolveState& u = p.us[pair];
+    // spectrum bound g of this solve from the density range of the state, with 5 % margin
+    unsigned* rg = p.range + pair * 2 * kRangeSlots;
+    float flo = 3.0e38f, fhi = 0.f;
+    for (int k = 0; k < kRangeSlots; ++k) {
+        flo = fminf(flo, __uint_as_float(rg[k]));
+        fhi = fmaxf(fhi, __uint_as_float(rg[kRangeSlots + k]));
+        rg[k] = 0x7f7fffffu;  // reset for the next state
+        rg[kRangeSlots + k] = 0u;
+    }
+    double lo = flo, hi = fhi;
+    if (!(lo > 0.0 && hi >= lo && hi < 1e30)) lo = hi = p.rho0;
+    double g = 0.0;
+    for (int k = 0; k <= 16; ++k) g = fmax(g, frozen_gain(p, lo + (hi - lo) * k / 16.0));
+    g = fmin(0.95, 1.05 * g);
+    u.gain = g;
+    u.cheb_delta = 0.5 * g;
+    u.cheb_sigma = (1.0 - 0.5 * g) / (0.5 * g);
     u.iter = 0;
     u.resid_bits = 0ull;
     u.jmax_bits = 0ull;
     u.converged = 0;
     u.running = 1;
+    u.resid_min = 1e300;
+    if (p.cheb) {  // first Chebyshev step: x += r / theta
+        u.mode = 1;
+        u.cheb_rho = 1.0 / u.cheb_sigma;
+        u.c1 = 0.0;
+        u.c2 = 1.0 / (1.0 - 0.5 * g);
+    } else {       // plain relaxation x += omega r (omega = 0: 2/(2 - g))
+        u.mode = 0;
+        u.c1 = 0.0;
+        u.c2 = p.omega > 0.0 ? p.omega : 2.0 / (2.0 - g);
+    }
 }
 
 // One thread: the S6 test, the S7 swap, and the loop condition of the graph.
@@ -461,6 +530,20 @@ static __global__ void k_us_ctl(DevSim p, int pair, cudaGraphConditionalHandle h
     else if (stop && !conv) atomicOr(p.status, STB_USOLVE_CAP);
     u.resid_bits = 0ull;
     u.jmax_bits = 0ull;
+    // coefficients of the next sweep (Chebyshev semi-iteration for the real spectrum
+    // [1 - g, 1] of I - A); a residual four times above the best one so far means the
+    // spectral bound was too small: continue with plain relaxation
+    if (u.mode == 1 && !bad && r > 4.0 * u.resid_min) u.mode = 0;
+    if (u.mode == 1) {
+        const double rn = 1.0 / (2.0 * u.cheb_sigma - u.cheb_rho);
+        u.c1 = rn * u.cheb_rho;
+        u.c2 = 2.0 * rn / u.cheb_delta;
+        u.cheb_rho = rn;
+    } else if (p.cheb) {  // fell back from Chebyshev: plain sweeps
+        u.c1 = 0.0;
+        u.c2 = 1.0;
+    }
+    u.resid_min = r < u.resid_min ? r : u.resid_min;
     if (stop) {
         u.iters_last = u.iter;
         u.iters_max = u.iter > u.iters_max ? u.iter : u.iters_max;
@@ -477,10 +560,10 @@ static __global__ void k_us_ctl(DevSim p, int pair, cudaGraphConditionalHandle h
 template <int LAT, typename T>
 __device__ __forceinline__ void collision_consts(const DevSim& p, T& k1, T& k2, T& k3)
 {
-    const double g = p.gamma;
-    k1 = T(-0.25 * (g + 1.0) * (g + 1.0) / (g - 1.0));       // -(h^2/4)(g+1)^2/(g-1)
-    k2 = T((1.0 / 6.0) * (g * g + 4.0 * g + 1.0) / (g - 1.0));  // (h^2/6)(g^2+4g+1)/(g-1)
-    k3 = T((1.0 / 3.0) * (g * g + 4.0 * g + 1.0) / (g + 1.0));  // (h/3)(g^2+4g+1)/(g+1)
+    const Phys<T>& q = phys<T>(p);
+    k1 = q.k1;  // -(h^2/4)(g+1)^2/(g-1)
+    k2 = q.k2;  // (h^2/6)(g^2+4g+1)/(g-1)
+    k3 = q.k3;  // (h/3)(g^2+4g+1)/(g+1)
 }
 
 // S10 results at one site -> A = (p - rho p') div u, B_ab = p(d_a u_b + d_b u_a),
@@ -521,7 +604,7 @@ __device__ __forceinline__ void derivs_tail(const DevSim& p, long long s, const 
     // X(a,b;c) = d_c(p u_a u_b) + delta_ab [p d_c(p/rho) + (p - rho p') u_c div u]
     auto PUU = [&](int c, int a, int b) { return a <= b ? dpuu[c][a][b] : dpuu[c][b][a]; };
     auto X = [&](int a, int b, int c) { return PUU(c, a, b) + (a == b ? P * dpr[c] + PM * u[c] * divu : T(0)); };
-    const T cj = T((1.0 - p.gamma) * p.cs0);
+    const T cj = phys<T>(p).cj;  // (1 - gamma) c_s^2(rho0)
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
@@ -544,10 +627,11 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
     using C = Codec<S>;
     constexpr int D = L::D;
     const long long s = r.s;
-    const T rs = T(p.rho0) + drs;
+    const Phys<T>& q = phys<T>(p);
+    const T rs = q.rho0 + drs;
     T cs2, dcs2;
     cs2_delta<T>(p, drs, cs2, dcs2);
-    const T cs0 = T(p.cs0);
+    const T cs0 = q.cs0;
     T trS = T(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) trS += Sig[a][a];
@@ -567,20 +651,16 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
 #pragma unroll
     for (int k = 0; k < L::NSHELL; ++k) {
         wl[k] = weight<LAT, T>(k, cs2);
-        w0[k] = T(p.w0[k]);
+        w0[k] = q.w0[k];
         // n^eq - w(rho0) rho0 = w rho X + w drho + rho0 (w(s) - w(s0)), and
         // w(s) - w(s0) = (s - s0) [c1 + c2 (s + s0) + c3 (s^2 + s s0 + s0^2)]
-        dw0[k] = C::DEV ? wl[k] * drs + T(p.rho0) * dcs2 *
+        dw0[k] = C::DEV ? wl[k] * drs + q.rho0 * dcs2 *
                                            (T(Lat<LAT>::wc(k, 1)) + T(Lat<LAT>::wc(k, 2)) * (cs2 + cs0) +
                                             T(Lat<LAT>::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0))
                         : T(0);
     }
-    const T g = T(p.gamma);
-    const T ics0 = T(1) / cs0;
-    const T cf_int = T(0.5 * (1.0 + p.gamma)) * ics0;
-    const T cf_jt = T(p.gamma - 1.0) * ics0;
-    const T cf_h2 = T(0.5) * ics0 * ics0;
-    const T cf_h3 = T(1.0 / 6.0) * ics0 * ics0 * ics0;
+    const T g = q.gamma;
+    const T cf_int = q.cf_int, cf_jt = q.cf_jt, cf_h2 = q.cf_h2, cf_h3 = q.cf_h3;
     // wrapped destination offsets (site indices < 2^31) for the shifts -4, -2, -1, 0, 1, 2, 4
     // that the velocity components take
     int ox[7], oy[7], oz[7];
@@ -639,7 +719,7 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
         float th = float(drs), tl = cp<float>(p.rho_lo)[s];  // the exact pre-collision sum
         if (!C::DEV) {
             float e;
-            two_sum(th, float(p.rho0), th, e);
+            two_sum(th, p.pf.rho0, th, e);
             tl = __fadd_rn(tl, e);
         }
         float rh, e;
@@ -700,9 +780,11 @@ __device__ __forceinline__ T d1p(const T* const (&pl)[5], int a, int i, int PX, 
     return T(2.0 / 3.0) * (g(pl[3], i) - g(pl[1], i)) - T(1.0 / 12.0) * (g(pl[4], i) - g(pl[0], i));
 }
 
-// S3-S6 fused: one Jacobi sweep of the u-solve.  Stage U (halo 4): u = (j0' + j~)/rho;
-// stage Q (halo 2): d_a u_b and q_ab; stage J (tile): j~new = -(1/12) d_b q_ab and the
-// S6 difference.  j~new = j~ + omega (J - j~) (omega = 1 is the plain iteration).
+// S3-S6 fused: one sweep of the u-solve, iterated in u = (j0' + j~)/rho (the same iteration
+// as in j~, which the paper uses).  Stage U (halo 4): u and rho - rho0 into the ring;
+// stage Q (halo 2): d_a u_b and q_ab; stage J (tile): j~new = -(1/12) d_b q_ab,
+// J(u) = (j0' + j~new)/rho, the update d = c1 d_prev + c2 (J(u) - u), u += d, and the
+// S6 difference rho |d| = |j~new - j~| of the resulting j~ iterates.
 template <int LAT, typename T, typename U>
 __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_sweep(DevSim p, int pair)
 {
@@ -723,14 +805,16 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_sweep(DevSim p, 
     const T* drho = cp<T>(p.rho);
     const T* j0p = cp<T>(p.j0p);
     const int cur = p.us[pair].cur;
-    const U* jold = cp<U>(p.jt[pair][cur]);
-    U* jnew = mp<U>(p.jt[pair][cur ^ 1]);
-    const U omega = U(p.omega);
+    const U* uold = cp<U>(p.uit[pair][cur]);
+    U* unew = mp<U>(p.uit[pair][cur ^ 1]);
+    const U c1 = U(p.us[pair].c1), c2 = U(p.us[pair].c2);  // this sweep's update (see k_us_ctl)
+    U* dvec = mp<U>(p.dvec[pair]);
+    const bool use_d = c1 != U(0), keep_d = p.cheb != 0;
     U dmax = U(0), jmax = U(0);  // residual reductions in the sweep's own precision
     bool bad = false;
     // stage U inputs of one plane, fetched one plane ahead into registers
     constexpr int MU = (UX * UY + TL::THREADS - 1) / TL::THREADS;
-    T pr[MU], pj[MU][3];
+    T pr[MU];
     U pt[MU][3];
     auto fetch = [&](int zl) {
         const int gz = D == 3 ? wrapc(zl, p.nz) : 0;
@@ -742,7 +826,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_sweep(DevSim p, 
                 const long long g = at(p, wrapc(x0 - 4 + ix, p.nx), wrapc(y0 - 4 + iy, p.ny), gz);
                 pr[m] = drho[g];
 #pragma unroll
-                for (int a = 0; a < D; ++a) { pj[m][a] = j0p[a * p.N + g]; pt[m][a] = jold[a * p.N + g]; }
+                for (int a = 0; a < D; ++a) pt[m][a] = uold[a * p.N + g];
             }
         }
     };
@@ -754,11 +838,9 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_sweep(DevSim p, 
             for (int m = 0; m < MU; ++m) {
                 const int k = tid + m * nth;
                 if (k < UX * UY) {
-                    const U dr = U(pr[m]);
-                    const U rho = U(p.rho0) + dr;
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) dst[a * UY * UX + k] = a < D ? (U(pj[m][a]) + pt[m][a]) / rho : U(0);
-                    dst[3 * UY * UX + k] = dr;
+                    for (int a = 0; a < 3; ++a) dst[a * UY * UX + k] = a < D ? pt[m][a] : U(0);
+                    dst[3 * UY * UX + k] = U(pr[m]);
                 }
             }
             if (zl + 1 < z1 + HZ) fetch(zl + 1);
@@ -778,7 +860,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_sweep(DevSim p, 
                     for (int a = 0; a < D; ++a)
                         du[a][b] = d1p<U>(pl, a, ui, UX, [&](const U* P, int j) { return P[b * UY * UX + j]; });
                 U P, DP, PM, RPP;
-                eos_full<U>(p, U(p.rho0) + pl[2][3 * UY * UX + ui], P, DP, PM, RPP);
+                eos_full<U>(p, phys<U>(p).rho0 + pl[2][3 * UY * UX + ui], P, DP, PM, RPP);
                 U div = U(0);
 #pragma unroll
                 for (int a = 0; a < D; ++a) div += du[a][a];
@@ -796,11 +878,15 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_sweep(DevSim p, 
             const int gz = D == 3 ? zj : 0;
             const U* ql[5];
             ring_planes<D, U>(sq, NQ * QY * QX, zj, ql);
+            const U* uc = su + ring_slot<D>(zj) * 4 * UY * UX;  // the tile's own u and rho - rho0
             for (int k = tid; k < TX * TY; k += nth) {
                 const int ix = k % TX, iy = k / TX;
                 const int gx = x0 + ix, gy = y0 + iy;
                 if (gx >= p.nx || gy >= p.ny) continue;
                 const long long g = at(p, gx, gy, gz);
+                const int ui = (iy + 4) * UX + ix + 4;
+                const U rho = phys<U>(p).rho0 + uc[3 * UY * UX + ui];
+                const U irho = U(1) / rho;
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
                     U acc = U(0);
@@ -809,16 +895,23 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_sweep(DevSim p, 
                         const int c = sym2<D>(a, b);
                         acc += d1p<U>(ql, b, (iy + 2) * QX + ix + 2, QX, [&](const U* P, int j) { return P[c * QY * QX + j]; });
                     }
-                    const U jt_old = jold[a * p.N + g];
-                    const U v = jt_old + omega * (-(U(1) / U(12)) * acc - jt_old);
-                    jnew[a * p.N + g] = v;
-                    const U dv = fabs(v - jt_old);
+                    const U jt_new = -(U(1) / U(12)) * acc;  // S5
+                    const U u_old = uc[a * UY * UX + ui];
+                    // residual of the fixed point u = (j0' + j~(u))/rho, the update d, u += d
+                    const U res = (U(j0p[a * p.N + g]) + jt_new) * irho - u_old;
+                    U d = c2 * res;
+                    if (use_d) d += c1 * dvec[a * p.N + g];
+                    if (keep_d) dvec[a * p.N + g] = d;
+                    unew[a * p.N + g] = u_old + d;
+                    const U dv = fabs(rho * d);  // |j~new - j~| of the j~ iterates
                     bad |= !(dv == dv);
                     dmax = fmax(dmax, dv);
-                    jmax = fmax(jmax, fabs(v));
+                    jmax = fmax(jmax, fabs(jt_new));
                 }
             }
         }
+        // stage J read the ring slot of plane zl - 4, which stage U of the next plane overwrites
+        if (D == 3) __syncthreads();
     }
     // NaN -> +inf, which orders above every finite residual
     const double dmax_d = bad ? __longlong_as_double(0x7ff0000000000000ll) : double(dmax);
@@ -845,9 +938,9 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
     const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
     const T* drho = cp<T>(p.rho);
     const T* j0p = cp<T>(p.j0p);
-    const U* jt = cp<U>(p.jt[0][p.us[0].cur]);
+    const U* uu = cp<U>(p.uit[0][p.us[0].cur]);  // S8: the converged u
     constexpr int MR = (RX * RY + TL::THREADS - 1) / TL::THREADS;
-    T pr[MR], pj[MR][3];
+    T pr[MR];
     U pt[MR][3];
     auto fetch = [&](int zl) {
         const int gz = D == 3 ? wrapc(zl, p.nz) : 0;
@@ -859,7 +952,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
                 const long long g = at(p, wrapc(x0 - 2 + ix, p.nx), wrapc(y0 - 2 + iy, p.ny), gz);
                 pr[m] = drho[g];
 #pragma unroll
-                for (int a = 0; a < D; ++a) { pj[m][a] = j0p[a * p.N + g]; pt[m][a] = jt[a * p.N + g]; }
+                for (int a = 0; a < D; ++a) pt[m][a] = uu[a * p.N + g];
             }
         }
     };
@@ -871,9 +964,9 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
             for (int m = 0; m < MR; ++m) {
                 const int k = tid + m * nth;
                 if (k < RX * RY) {
-                    const T rho = T(p.rho0) + pr[m];
+                    const T rho = phys<T>(p).rho0 + pr[m];
 #pragma unroll
-                    for (int a = 0; a < 3; ++a) dst[a * RY * RX + k] = a < D ? (pj[m][a] + T(pt[m][a])) / rho : T(0);
+                    for (int a = 0; a < 3; ++a) dst[a * RY * RX + k] = a < D ? T(pt[m][a]) : T(0);
                     const T P = eos_p<T>(p, rho);
                     dst[3 * RY * RX + k] = rho;
                     dst[4 * RY * RX + k] = P;
@@ -914,10 +1007,11 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
                 }
                 const long long s = at(p, gx, gy, gz);
                 const T u[3] = {pl[2][ri], pl[2][PS + ri], pl[2][2 * PS + ri]};
-                T jtl[3] = {T(0), T(0), T(0)};
+                const T rs = pl[2][3 * PS + ri];
+                T jtl[3] = {T(0), T(0), T(0)};  // j~ = rho u - j0' (S8)
 #pragma unroll
-                for (int a = 0; a < D; ++a) jtl[a] = T(jt[a * p.N + s]);
-                derivs_tail<LAT, T>(p, s, du, divj, dp, dpr, dpuu, pl[2][3 * PS + ri], u, jtl);
+                for (int a = 0; a < D; ++a) jtl[a] = rs * u[a] - j0p[a * p.N + s];
+                derivs_tail<LAT, T>(p, s, du, divj, dp, dpr, dpuu, rs, u, jtl);
             }
         }
         __syncthreads();
@@ -947,7 +1041,8 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
     const T* drho = cp<T>(p.rho);
     const T* j0p = cp<T>(p.j0p);
     const T* fp = cp<T>(p.f);
-    const U* jt = cp<U>(p.jt[0][p.us[0].cur]);
+    const U* uu = cp<U>(p.uit[0][p.us[0].cur]);
+    U* jw = mp<U>(p.jt_warm);
     T k1, k2, k3;
     collision_consts<LAT, T>(p, k1, k2, k3);
     constexpr int MR = (RX * RY + TL::THREADS - 1) / TL::THREADS;
@@ -993,12 +1088,15 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
                 r.x = gx; r.y = gy; r.z = gz; r.s = at(p, gx, gy, gz);
                 const long long s = r.s;
                 const T drs = drho[s];
-                const T rs = T(p.rho0) + drs;
+                const T rs = phys<T>(p).rho0 + drs;
                 T u[3] = {T(0), T(0), T(0)}, f[3] = {T(0), T(0), T(0)}, jtl[3] = {T(0), T(0), T(0)};
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
-                    jtl[a] = T(jt[a * p.N + s]);
-                    u[a] = (j0p[a * p.N + s] + jtl[a]) / rs;
+                    const U ua = uu[a * p.N + s];
+                    u[a] = T(ua);
+                    const U jta = U(rs) * ua - U(j0p[a * p.N + s]);  // j~ = rho u - j0' (S8)
+                    jtl[a] = T(jta);
+                    jw[a * p.N + s] = jta;  // the next step's warm start
                     f[a] = fp[a * p.N + s];
                 }
                 T P, DP, PM, RPP;
@@ -1060,7 +1158,7 @@ __global__ void k_init_eq(DevSim p, const double* rho_in, const double* u_in, in
     const T drs = T(rho_in[s] - p.rho0);
     T cs2, dcs2;
     cs2_delta<T>(p, drs, cs2, dcs2);
-    const T cs0 = T(p.cs0);
+    const T cs0 = phys<T>(p).cs0;
     const T ics2 = T(1) / cs2;
     T uu = T(0);
 #pragma unroll
@@ -1073,7 +1171,7 @@ __global__ void k_init_eq(DevSim p, const double* rho_in, const double* u_in, in
         const T X = uc * ics2 + T(0.5) * uc * uc * ics2 * ics2 - T(0.5) * uu * ics2;
         const T w = weight<LAT, T>(k, cs2);
         const T dev = w * rs * X + w * drs +
-                      T(p.rho0) * dcs2 *
+                      phys<T>(p).rho0 * dcs2 *
                           (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) + T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
         stored_sum += double(pop_put<S, T>(p, dst, i, s, C::DEV ? dev : w * rs * (T(1) + X)));
     }
@@ -1088,13 +1186,12 @@ __global__ void k_fields_out(DevSim p, int pair, double* rho_out, double* u_out)
     using L = Lat<LAT>;
     const long long s = gtid();
     if (s >= p.N) return;
-    const T rs = T(p.rho0) + cp<T>(p.rho)[s];
-    const U* jt = cp<U>(p.jt[pair][p.us[pair].cur]);
+    const T rs = phys<T>(p).rho0 + cp<T>(p.rho)[s];
+    const U* uu = cp<U>(p.uit[pair][p.us[pair].cur]);
     if (rho_out) rho_out[s] = double(rs);
     if (u_out)
 #pragma unroll
-        for (int a = 0; a < L::D; ++a)
-            u_out[a * p.N + s] = double((cp<T>(p.j0p)[a * p.N + s] + T(jt[a * p.N + s])) / rs);
+        for (int a = 0; a < L::D; ++a) u_out[a * p.N + s] = double(uu[a * p.N + s]);
 }
 
 template <int LAT, int S>
@@ -1174,18 +1271,6 @@ static __global__ void k_red_final(DevSim p, const double* part, int nparts, dou
     if (threadIdx.x < 4) out[threadIdx.x] = sm[threadIdx.x][0];
 }
 
-template <int LAT, typename U>
-__global__ void k_copy_jt(DevSim p)
-{
-    using L = Lat<LAT>;
-    const long long s = gtid();
-    if (s >= p.N) return;
-    const U* src = cp<U>(p.jt[0][p.us[0].cur]);
-    U* dst = mp<U>(p.jt[1][0]);
-#pragma unroll
-    for (int a = 0; a < L::D; ++a) dst[a * p.N + s] = src[a * p.N + s];
-}
-
 // ---------------------------------------------------------------------------
 // Kernel table of one combination
 // ---------------------------------------------------------------------------
@@ -1194,7 +1279,7 @@ KernelTable make_table(bool read_pops)
 {
     KernelTable t{};
     t.moments = (const void*)k_moments<LAT, T, S, U>;
-    t.force = (const void*)k_force<LAT, T>;
+    t.force = (const void*)k_force<LAT, T, U>;
     t.us_begin = (const void*)k_us_begin;
     t.sweep = (const void*)k_sweep<LAT, T, U>;
     t.us_ctl = (const void*)k_us_ctl;
@@ -1206,7 +1291,6 @@ KernelTable make_table(bool read_pops)
     t.pops_in = (const void*)k_pops_in<LAT, S>;
     t.red_partial = (const void*)k_red_partial<LAT, S>;
     t.red_final = (const void*)k_red_final;
-    t.copy_jt = (const void*)k_copy_jt<LAT, U>;
     t.block = 256;
     using TL = Tile<Lat<LAT>::D>;
     t.tile[0] = TL::TX;

@@ -42,7 +42,8 @@ class lbm_params(ctypes.Structure):
                 ("storage", ctypes.c_int), ("usolve_precision", ctypes.c_int), ("usolve_tol", ctypes.c_double),
                 ("usolve_rtol", ctypes.c_double), ("usolve_max_iter", ctypes.c_int),
                 ("usolve_warm_start", ctypes.c_int), ("rho_check_min", ctypes.c_double),
-                ("rho_check_max", ctypes.c_double), ("usolve_omega", ctypes.c_double)]
+                ("rho_check_max", ctypes.c_double), ("usolve_omega", ctypes.c_double),
+                ("usolve_chebyshev", ctypes.c_int)]
 
 
 class lbm_stats(ctypes.Structure):
@@ -289,6 +290,6 @@ def make_eos(kind=LBM_EOS_VDW, a=0.0, b=0.0, T=0.0, rho1=0.0, rho2=0.0, A=0.0, c
 
 def make_params(gamma=0.0, kappa=0.0, rho0=1.0, storage=LBM_STORE_F32, usolve_precision=LBM_USOLVE_NATIVE,
                 usolve_tol=0.0, usolve_rtol=0.0, usolve_max_iter=0, usolve_warm_start=1,
-                rho_check_min=0.0, rho_check_max=0.0, usolve_omega=1.0):
+                rho_check_min=0.0, rho_check_max=0.0, usolve_omega=1.0, usolve_chebyshev=0):
     return lbm_params(gamma, kappa, rho0, storage, usolve_precision, usolve_tol, usolve_rtol, usolve_max_iter,
-                      usolve_warm_start, rho_check_min, rho_check_max, usolve_omega)
+                      usolve_warm_start, rho_check_min, rho_check_max, usolve_omega, usolve_chebyshev)

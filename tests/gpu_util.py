@@ -9,13 +9,14 @@ ORACLE_TOL = 1e-14
 
 
 def lib_sim(case, storage=P.LBM_STORE_F64, usolve=P.LBM_USOLVE_NATIVE, tol=0.0, rtol=0.0, warm=1, maxit=0,
-            stream=None, omega=1.0):
+            stream=None, omega=1.0, chebyshev=0):
     """The case on the CUDA library; omega = 1 is the plain iteration of the paper, 0 the automatic one."""
     a, b, T = case.eos_abT
     eos = P.make_eos(P.LBM_EOS_VDW, a=a, b=b, T=T)
     prm = P.make_params(gamma=case.gamma, kappa=case.kappa, rho0=case.rho0, storage=storage, usolve_precision=usolve,
                         usolve_tol=tol, usolve_rtol=rtol, usolve_max_iter=maxit, usolve_warm_start=warm,
-                        rho_check_min=0.98 * case.eos.rho_g, rho_check_max=1.02 * case.eos.rho_l, usolve_omega=omega)
+                        rho_check_min=0.98 * case.eos.rho_g, rho_check_max=1.02 * case.eos.rho_l, usolve_omega=omega,
+                        usolve_chebyshev=chebyshev)
     return P.Sim(case.lattice, case.dims, eos, prm, stream)
 
 

@@ -80,10 +80,12 @@ def test_fp64_parity_with_flow_and_gamma():
 
 
 @pytest.mark.parametrize("name,dims", [("droplet2d", (48, 40)), ("droplet3d", (16, 18, 17))])
-def test_fp64_over_relaxed_usolve_reaches_the_same_fixed_point(name, dims):
-    """omega = 2/(2 - g) (automatic) converges to the fixed point of the plain iteration."""
+@pytest.mark.parametrize("cheb", [0, 1])
+def test_fp64_accelerated_usolve_reaches_the_same_fixed_point(name, dims, cheb):
+    """omega = 2/(2 - g) relaxation and Chebyshev acceleration converge to the fixed point of the
+    plain iteration of Sec. IX (the oracle's), in fewer sweeps."""
     case = W.make_case(name, dims=dims)
-    g = lib_sim(case, omega=0.0)
+    g = lib_sim(case, omega=0.0, chebyshev=cheb)
     o = oracle_sim(case)
     g.init(case.rho)
     o.init(case.rho)
@@ -91,6 +93,7 @@ def test_fp64_over_relaxed_usolve_reaches_the_same_fixed_point(name, dims):
     o.step(6)
     idx = perm_to_oracle(case.lattice)
     assert rel_linf(g.populations()[idx], o.pops()) < 1e-12
+    assert g.stats().usolve_iters_last < o.last_iters()
 
 
 def test_fp64_cold_start_usolve():
