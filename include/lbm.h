@@ -119,7 +119,8 @@ typedef struct {
 
 /* Create a simulation on the current CUDA device.
  *   lattice: LBM_D2Q21 or LBM_D3Q59.  dims[3] = {nx, ny, nz}, periodic in every
- *   direction; each of nx, ny (and nz in 3D) must be >= 4; nz must be 1 in 2D.
+ *   direction; each of nx, ny (and nz in 3D) must be >= 4; nz must be 1 in 2D;
+ *   nx*ny*nz < 2^31 sites and ny <= 524280.
  *   cuda_stream: a cudaStream_t (may be NULL for the legacy default stream).
  *   Fails with LBM_E_INVALID_ARG on bad arguments, LBM_E_BULKVISC or LBM_E_WEIGHTS
  *   when the EOS check over [rho_check_min, rho_check_max] fails, LBM_E_OOM when

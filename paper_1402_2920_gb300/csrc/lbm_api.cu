@@ -192,6 +192,9 @@ int validate(int lattice, const int64_t dims[3], int storage)
     const double N = double(dims[0]) * double(dims[1]) * double(dims[2]);
     const int Q = lattice == LBM_D3Q59 ? 59 : 21;
     if (N * Q > 9.0e18 / 8.0) return LBM_E_INVALID_ARG;
+    // site indices inside a plane stack are 32-bit in the streaming kernel; the tiled
+    // kernels' grid has ceil(ny / 16) <= 65535 rows
+    if (N >= 2147483648.0 || dims[1] > 65535 * 8) return LBM_E_INVALID_ARG;
     return LBM_OK;
 }
 

@@ -192,6 +192,12 @@ __device__ __forceinline__ void cs2_delta(const DevSim& p, T drho, T& s, T& ds)
 // shift of at most 4.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int wrapc(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+// v mod n in [0, n) for any v (tile halos of small lattices wrap more than once)
+__device__ __forceinline__ int wrapm(int v, int n)
+{
+    v %= n;
+    return v < 0 ? v + n : v;
+}
 
 struct Site {
     int x, y, z;
@@ -780,28 +786,69 @@ __device__ __forceinline__ T d1p(const T* const (&pl)[5], int a, int i, int PX, 
     return T(2.0 / 3.0) * (g(pl[3], i) - g(pl[1], i)) - T(1.0 / 12.0) * (g(pl[4], i) - g(pl[0], i));
 }
 
+// Asynchronous element copy global -> shared (cp.async); completion is tracked per thread in
+// commit groups, and a barrier after cp.async.wait_group publishes the data to the CTA.
+template <int B>
+__device__ __forceinline__ void cp_async(void* sdst, const void* gsrc)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
+    if (B == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+    else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Shared-memory plan of the sweep: a ring of R planes of u (sweep precision) and rho - rho0
+// (storage precision) with in-plane halo 4, PF of them in flight, and the q planes, which
+// share the row pitch UX of the ring so that a warp's stage-Q reads fall in distinct banks.
+template <int D, typename T, typename U>
+struct SweepPlan {
+    using TL = Tile<D>;
+    static constexpr int UX = TL::TX + 8, UY = TL::TY + 8, UP = UX * UY;
+    static constexpr int QX = TL::TX + 4, QY = TL::TY + 4, QP = QY * UX;
+    static constexpr int NQ = D == 3 ? 6 : 3;
+    static constexpr int PF = D == 3 ? 2 : 0;      // planes fetched ahead
+    static constexpr int R = D == 3 ? 5 + PF : 1;  // ring planes
+    static constexpr int NQB = D == 3 ? 2 : 1;     // q plane buffers
+    static constexpr size_t OFF_Q = size_t(R) * D * UP * sizeof(U);
+    static constexpr size_t OFF_R = (OFF_Q + size_t(NQB) * NQ * QP * sizeof(U) + 15) / 16 * 16;
+    static constexpr size_t BYTES = OFF_R + size_t(R) * UP * sizeof(T);
+};
+
 // S3-S6 fused: one sweep of the u-solve, iterated in u = (j0' + j~)/rho (the same iteration
-// as in j~, which the paper uses).  Stage U (halo 4): u and rho - rho0 into the ring;
-// stage Q (halo 2): d_a u_b and q_ab; stage J (tile): j~new = -(1/12) d_b q_ab,
-// J(u) = (j0' + j~new)/rho, the update d = c1 d_prev + c2 (J(u) - u), u += d, and the
-// S6 difference rho |d| = |j~new - j~| of the resulting j~ iterates.
+// as in j~, which the paper uses).  The CTA marches along z; per plane zl (two barriers):
+//   fetch    plane zl + PF of u and rho - rho0 (in-plane halo 4) into the ring, asynchronously;
+//   stage Q  q_ab of plane zq = zl - 2 (in-plane halo 2; the z derivatives read the ring)
+//            into one of two plane buffers;
+//   stage J  at the thread's own site: the in-plane part d_x q_ax + d_y q_ay of plane zq, and
+//            q_az(zq) scattered into the z-derivative sums of planes zq-2 .. zq+2, which live
+//            in registers.  Plane zq - 2 is then complete: j~new = -(1/12) d_b q_ab (S5),
+//            J(u) = (j0' + j~new)/rho, the update d = c1 d_prev + c2 (J(u) - u), u += d, and
+//            the S6 difference rho |d| = |j~new - j~| of the resulting j~ iterates.
+// In 2D the march is the single plane and the J stage finishes it directly.
 template <int LAT, typename T, typename U>
-__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_sweep(DevSim p, int pair)
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2 : 1) k_sweep(DevSim p, int pair)
 {
     using L = Lat<LAT>;
     constexpr int D = L::D;
     using TL = Tile<D>;
-    constexpr int TX = TL::TX, TY = TL::TY, NZR = TL::NZR;
-    constexpr int UX = TX + 8, UY = TY + 8, QX = TX + 4, QY = TY + 4;
-    constexpr int NQ = D == 3 ? 6 : 3;
+    using SP = SweepPlan<D, T, U>;
+    constexpr int TX = TL::TX, TY = TL::TY, NT = TL::THREADS;
+    constexpr int UX = SP::UX, UP = SP::UP, QX = SP::QX, QY = SP::QY, QP = SP::QP, NQ = SP::NQ;
+    constexpr int PF = SP::PF, R = SP::R;
     constexpr int HZ = D == 3 ? 4 : 0;
+    static_assert(TX * TY == NT, "one J site per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    U* su = reinterpret_cast<U*>(smem_raw);  // [NZR][4][UY][UX]: u_x, u_y, u_z, rho - rho0
-    U* sq = su + NZR * 4 * UY * UX;          // [NZR][NQ][QY][QX]
-    const int tid = threadIdx.x, nth = blockDim.x;
+    U* su = reinterpret_cast<U*>(smem_raw);             // [R][D][UP]: u
+    U* sq = reinterpret_cast<U*>(smem_raw + SP::OFF_Q);  // [NQB][NQ][QP]: q_ab
+    T* sr = reinterpret_cast<T*>(smem_raw + SP::OFF_R);  // [R][UP]: rho - rho0
+    auto slot = [](int z) { return D == 3 ? (z + 8 * R) % R : 0; };  // z >= -8
+    const int tid = threadIdx.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
     const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
+    const long long NP = (long long)p.nx * p.ny;  // sites per plane
     const T* drho = cp<T>(p.rho);
     const T* j0p = cp<T>(p.j0p);
     const int cur = p.us[pair].cur;
@@ -810,109 +857,170 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_sweep(DevSim p, 
     const U c1 = U(p.us[pair].c1), c2 = U(p.us[pair].c2);  // this sweep's update (see k_us_ctl)
     U* dvec = mp<U>(p.dvec[pair]);
     const bool use_d = c1 != U(0), keep_d = p.cheb != 0;
+    // the thread's own site (stage J)
+    const int ix = tid % TX, iy = tid / TX;
+    const int gx = x0 + ix, gy = y0 + iy;
+    const bool own = gx < p.nx && gy < p.ny;
+    const long long own_xy = (long long)gy * p.nx + gx;
     U dmax = U(0), jmax = U(0);  // residual reductions in the sweep's own precision
     bool bad = false;
-    // stage U inputs of one plane, fetched one plane ahead into registers
-    constexpr int MU = (UX * UY + TL::THREADS - 1) / TL::THREADS;
-    T pr[MU];
-    U pt[MU][3];
+    // in-plane offsets of the thread's halo points, wrapped once (true modulo: the halo of a
+    // small lattice may exceed it)
+    constexpr int MU = (UP + NT - 1) / NT;
+    int hoff[MU];
+#pragma unroll
+    for (int m = 0; m < MU; ++m) {
+        const int k = tid + m * NT;
+        hoff[m] = k < UP ? wrapm(x0 - 4 + k % UX, p.nx) + p.nx * wrapm(y0 - 4 + k / UX, p.ny) : 0;
+    }
     auto fetch = [&](int zl) {
-        const int gz = D == 3 ? wrapc(zl, p.nz) : 0;
+        const long long base = D == 3 ? (long long)wrapc(zl, p.nz) * NP : 0;
+        U* du = su + slot(zl) * D * UP;
+        T* dr = sr + slot(zl) * UP;
 #pragma unroll
         for (int m = 0; m < MU; ++m) {
-            const int k = tid + m * nth;
-            if (k < UX * UY) {
-                const int ix = k % UX, iy = k / UX;
-                const long long g = at(p, wrapc(x0 - 4 + ix, p.nx), wrapc(y0 - 4 + iy, p.ny), gz);
-                pr[m] = drho[g];
+            const int k = tid + m * NT;
+            if (k < UP) {
+                const long long g = base + hoff[m];
 #pragma unroll
-                for (int a = 0; a < D; ++a) pt[m][a] = uold[a * p.N + g];
+                for (int a = 0; a < D; ++a) cp_async<sizeof(U)>(du + a * UP + k, uold + a * p.N + g);
+                cp_async<sizeof(T)>(dr + k, drho + g);
             }
         }
     };
-    fetch(z0 - HZ);
-    for (int zl = z0 - HZ; zl < z1 + HZ; ++zl) {
-        {  // stage U: plane zl from the registers, then fetch the next plane
-            U* dst = su + ring_slot<D>(zl) * 4 * UY * UX;
+    // stage J inputs of the own site (j0', previous update), fetched one plane ahead
+    U pj[3] = {U(0), U(0), U(0)}, pd[3] = {U(0), U(0), U(0)};
+    auto fetch_j = [&](int zj) {
+        if (own && zj >= z0 && zj < z1) {
+            const long long g = (D == 3 ? zj * NP : 0) + own_xy;
 #pragma unroll
-            for (int m = 0; m < MU; ++m) {
-                const int k = tid + m * nth;
-                if (k < UX * UY) {
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) dst[a * UY * UX + k] = a < D ? pt[m][a] : U(0);
-                    dst[3 * UY * UX + k] = U(pr[m]);
-                }
+            for (int a = 0; a < D; ++a) {
+                pj[a] = U(j0p[a * p.N + g]);
+                if (use_d) pd[a] = dvec[a * p.N + g];
             }
-            if (zl + 1 < z1 + HZ) fetch(zl + 1);
         }
-        __syncthreads();
+    };
+    // A[k][a]: sum over b of d_b q_ab at plane zq - 2 + k of the own site, as far as known
+    U A[5][3];
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) A[k][a] = U(0);
+    U ju[3] = {U(0), U(0), U(0)}, jr = U(0);  // own u and rho - rho0 of the plane being finished
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        fetch(z0 - HZ + k);
+        cp_async_commit();
+    }
+    fetch_j(z0);
+    for (int zl = z0 - HZ; zl < z1 + HZ; ++zl) {
+        // the ring slot of plane zl + PF held plane zl + PF - R, last read before the
+        // second barrier of the previous step
+        if (zl + PF < z1 + HZ) fetch(zl + PF);
+        cp_async_commit();
+        cp_async_wait<PF>();  // plane zl has landed (this thread's copies)
+        __syncthreads();      // ... and everyone's
+        const int zj = zl - HZ;  // the plane that stage J finishes in this step
+        if (zj >= z0 && zj < z1) {
+            // read before the second barrier: the next step's fetch may reuse this slot
+            const U* uc = su + slot(zj) * D * UP;
+            const int ui = (iy + 4) * UX + ix + 4;
+#pragma unroll
+            for (int a = 0; a < D; ++a) ju[a] = uc[a * UP + ui];
+            jr = U(sr[slot(zj) * UP + ui]);
+        }
         const int zq = zl - HZ / 2;
-        if (D == 2 || (zq >= z0 - 2 && zq < z1 + 2)) {  // stage Q: plane zq
+        const bool qplane = D == 2 || (zq >= z0 - 2 && zq < z1 + 2);
+        U* qb = sq + (D == 3 ? (zq & 1) : 0) * NQ * QP;
+        if (qplane) {  // stage Q: plane zq
             const U* pl[5];
-            ring_planes<D, U>(su, 4 * UY * UX, zq, pl);
-            for (int k = tid; k < QX * QY; k += nth) {
-                const int qx = k % QX, qy = k / QX;
-                const int ui = (qy + 2) * UX + qx + 2;
+#pragma unroll
+            for (int k = 0; k < 5; ++k) pl[k] = su + slot(D == 3 ? zq - 2 + k : 0) * D * UP;
+            const T* rq = sr + slot(zq) * UP;
+            for (int k = tid; k < QY * UX; k += NT) {
+                if (k % UX >= QX) continue;
+                const int ui = k + 2 * UX + 2;  // (qy + 2) UX + qx + 2
                 U du[3][3];
 #pragma unroll
                 for (int b = 0; b < D; ++b)
 #pragma unroll
                     for (int a = 0; a < D; ++a)
-                        du[a][b] = d1p<U>(pl, a, ui, UX, [&](const U* P, int j) { return P[b * UY * UX + j]; });
+                        du[a][b] = d1p<U>(pl, a, ui, UX, [&](const U* P, int j) { return P[b * UP + j]; });
                 U P, DP, PM, RPP;
-                eos_full<U>(p, phys<U>(p).rho0 + pl[2][3 * UY * UX + ui], P, DP, PM, RPP);
+                eos_full<U>(p, phys<U>(p).rho0 + U(rq[ui]), P, DP, PM, RPP);
                 U div = U(0);
 #pragma unroll
                 for (int a = 0; a < D; ++a) div += du[a][a];
-                U* dq = sq + ring_slot<D>(zq) * NQ * QY * QX;
 #pragma unroll
                 for (int a = 0; a < D; ++a)
 #pragma unroll
                     for (int b = a; b < D; ++b)
-                        dq[sym2<D>(a, b) * QY * QX + k] = (a == b ? PM * div : U(0)) + P * (du[b][a] + du[a][b]);
+                        qb[sym2<D>(a, b) * QP + k] = (a == b ? PM * div : U(0)) + P * (du[b][a] + du[a][b]);
             }
         }
         __syncthreads();
-        const int zj = zl - HZ;
-        if (zj >= z0 && zj < z1) {  // stage J: plane zj
-            const int gz = D == 3 ? zj : 0;
-            const U* ql[5];
-            ring_planes<D, U>(sq, NQ * QY * QX, zj, ql);
-            const U* uc = su + ring_slot<D>(zj) * 4 * UY * UX;  // the tile's own u and rho - rho0
-            for (int k = tid; k < TX * TY; k += nth) {
-                const int ix = k % TX, iy = k / TX;
-                const int gx = x0 + ix, gy = y0 + iy;
-                if (gx >= p.nx || gy >= p.ny) continue;
-                const long long g = at(p, gx, gy, gz);
-                const int ui = (iy + 4) * UX + ix + 4;
-                const U rho = phys<U>(p).rho0 + uc[3 * UY * UX + ui];
-                const U irho = U(1) / rho;
+        if (qplane) {  // stage J
+            const int qi = (iy + 2) * UX + ix + 2;
+            if (zq >= z0 && zq < z1) {  // in-plane derivatives of plane zq
+                const U* ql[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) ql[k] = qb;
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
                     U acc = U(0);
 #pragma unroll
-                    for (int b = 0; b < D; ++b) {
+                    for (int b = 0; b < 2; ++b) {
                         const int c = sym2<D>(a, b);
-                        acc += d1p<U>(ql, b, (iy + 2) * QX + ix + 2, QX, [&](const U* P, int j) { return P[c * QY * QX + j]; });
+                        acc += d1p<U>(ql, b, qi, UX, [&](const U* P, int j) { return P[c * QP + j]; });
                     }
-                    const U jt_new = -(U(1) / U(12)) * acc;  // S5
-                    const U u_old = uc[a * UY * UX + ui];
+                    A[2][a] += acc;
+                }
+            }
+            if (D == 3) {
+                // d_z g(z) = (2/3)(g(z+1) - g(z-1)) - (1/12)(g(z+2) - g(z-2)): the share of
+                // g(zq) = q_az(zq) in the planes zq-2 .. zq+2
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const U v = qb[sym2<D>(a, 2) * QP + qi];
+                    A[0][a] -= U(1.0 / 12.0) * v;
+                    A[1][a] += U(2.0 / 3.0) * v;
+                    A[3][a] -= U(2.0 / 3.0) * v;
+                    A[4][a] += U(1.0 / 12.0) * v;
+                }
+            }
+            constexpr int KC = D == 3 ? 0 : 2;  // the finished plane: zq - 2 (3D), zq (2D)
+            const int zc = D == 3 ? zq - 2 : zq;
+            if (own && zc >= z0 && zc < z1) {
+                const long long g = (D == 3 ? zc * NP : 0) + own_xy;
+                const U rho = phys<U>(p).rho0 + jr;
+                const U irho = U(1) / rho;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const U jt_new = -(U(1) / U(12)) * A[KC][a];  // S5
                     // residual of the fixed point u = (j0' + j~(u))/rho, the update d, u += d
-                    const U res = (U(j0p[a * p.N + g]) + jt_new) * irho - u_old;
+                    const U res = (pj[a] + jt_new) * irho - ju[a];
                     U d = c2 * res;
-                    if (use_d) d += c1 * dvec[a * p.N + g];
+                    if (use_d) d += c1 * pd[a];
                     if (keep_d) dvec[a * p.N + g] = d;
-                    unew[a * p.N + g] = u_old + d;
+                    unew[a * p.N + g] = ju[a] + d;
                     const U dv = fabs(rho * d);  // |j~new - j~| of the j~ iterates
                     bad |= !(dv == dv);
                     dmax = fmax(dmax, dv);
                     jmax = fmax(jmax, fabs(jt_new));
                 }
             }
+            if (D == 3) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) A[k][a] = A[k + 1][a];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) A[4][a] = U(0);
+            }
+            fetch_j(zc + 1);
         }
-        // stage J read the ring slot of plane zl - 4, which stage U of the next plane overwrites
-        if (D == 3) __syncthreads();
     }
+    cp_async_wait<0>();
     // NaN -> +inf, which orders above every finite residual
     const double dmax_d = bad ? __longlong_as_double(0x7ff0000000000000ll) : double(dmax);
     block_max2(dmax_d, double(jmax), &p.us[pair].resid_bits, &p.us[pair].jmax_bits);
@@ -940,16 +1048,21 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
     const T* j0p = cp<T>(p.j0p);
     const U* uu = cp<U>(p.uit[0][p.us[0].cur]);  // S8: the converged u
     constexpr int MR = (RX * RY + TL::THREADS - 1) / TL::THREADS;
+    int hoff[MR];  // wrapped in-plane offsets of the halo points
+#pragma unroll
+    for (int m = 0; m < MR; ++m) {
+        const int k = tid + m * nth;
+        hoff[m] = k < RX * RY ? wrapm(x0 - 2 + k % RX, p.nx) + p.nx * wrapm(y0 - 2 + k / RX, p.ny) : 0;
+    }
     T pr[MR];
     U pt[MR][3];
     auto fetch = [&](int zl) {
-        const int gz = D == 3 ? wrapc(zl, p.nz) : 0;
+        const long long base = D == 3 ? (long long)wrapc(zl, p.nz) * p.nx * p.ny : 0;
 #pragma unroll
         for (int m = 0; m < MR; ++m) {
             const int k = tid + m * nth;
             if (k < RX * RY) {
-                const int ix = k % RX, iy = k / RX;
-                const long long g = at(p, wrapc(x0 - 2 + ix, p.nx), wrapc(y0 - 2 + iy, p.ny), gz);
+                const long long g = base + hoff[m];
                 pr[m] = drho[g];
 #pragma unroll
                 for (int a = 0; a < D; ++a) pt[m][a] = uu[a * p.N + g];
@@ -1046,15 +1159,20 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
     T k1, k2, k3;
     collision_consts<LAT, T>(p, k1, k2, k3);
     constexpr int MR = (RX * RY + TL::THREADS - 1) / TL::THREADS;
+    int hoff[MR];  // wrapped in-plane offsets of the halo points
+#pragma unroll
+    for (int m = 0; m < MR; ++m) {
+        const int k = tid + m * nth;
+        hoff[m] = k < RX * RY ? wrapm(x0 - 2 + k % RX, p.nx) + p.nx * wrapm(y0 - 2 + k / RX, p.ny) : 0;
+    }
     T pa[MR][NP];
     auto fetch = [&](int zl) {
-        const int gz = D == 3 ? wrapc(zl, p.nz) : 0;
+        const long long base = D == 3 ? (long long)wrapc(zl, p.nz) * p.nx * p.ny : 0;
 #pragma unroll
         for (int m = 0; m < MR; ++m) {
             const int k = tid + m * nth;
             if (k < RX * RY) {
-                const int ix = k % RX, iy = k / RX;
-                const long long g = at(p, wrapc(x0 - 2 + ix, p.nx), wrapc(y0 - 2 + iy, p.ny), gz);
+                const long long g = base + hoff[m];
 #pragma unroll
                 for (int c = 0; c < NP; ++c) pa[m][c] = aux[(AL::A + c) * p.N + g];
             }
@@ -1298,7 +1416,7 @@ KernelTable make_table(bool read_pops)
     t.tile[2] = TL::ZB;
     t.tile_threads = TL::THREADS;
     constexpr int D = Lat<LAT>::D;
-    t.smem_sweep = size_t(TL::NZR) * (4 * (TL::TX + 8) * (TL::TY + 8) + (D == 3 ? 6 : 3) * (TL::TX + 4) * (TL::TY + 4)) * sizeof(U);
+    t.smem_sweep = SweepPlan<D, T, U>::BYTES;
     t.smem_derivs = size_t(TL::NZR) * 6 * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
     t.smem_collide = size_t(TL::NZR) * (1 + AuxLayout<D>::NB + D) * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
     cudaFuncSetAttribute(t.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_sweep));
