@@ -354,7 +354,7 @@ __device__ __forceinline__ void block_max2(double a, double b, unsigned long lon
 // S1: moments and the c_s^2 window check
 // ---------------------------------------------------------------------------
 template <int LAT, typename T, int S, typename U>
-__global__ void k_moments(DevSim p, int src, int pair)
+__global__ void __launch_bounds__(256, 3) k_moments(DevSim p, int src, int pair)
 {
     using L = Lat<LAT>;
     using C = Codec<S>;
@@ -368,14 +368,17 @@ __global__ void k_moments(DevSim p, int src, int pair)
         hi = r0.x;
         lo = r0.y;
     }
+    // all loads first, so that a warp keeps the whole column of Q planes in flight
+    T v[L::Q];
+#pragma unroll
+    for (int i = C::EXACT ? 1 : 0; i < L::Q; ++i) v[i] = pop_raw<S, T>(p, src, i, s);
 #pragma unroll
     for (int i = C::EXACT ? 1 : 0; i < L::Q; ++i) {
-        const T v = pop_raw<S, T>(p, src, i, s);
-        if (C::EXACT) acc2(hi, lo, float(v));
-        else sum += v;
-        if (L::cx(i)) j[0] += T(L::cx(i)) * v;
-        if (L::cy(i)) j[1] += T(L::cy(i)) * v;
-        if (L::cz(i)) j[2] += T(L::cz(i)) * v;
+        if (C::EXACT) acc2(hi, lo, float(v[i]));
+        else sum += v[i];
+        if (L::cx(i)) j[0] += T(L::cx(i)) * v[i];
+        if (L::cy(i)) j[1] += T(L::cy(i)) * v[i];
+        if (L::cz(i)) j[2] += T(L::cz(i)) * v[i];
     }
     // rho - rho0: the deviation sum itself (sum_i w_i(rho0) rho0 = rho0 and the
     // odd offsets cancel in j0), or sum - rho0
@@ -623,7 +626,24 @@ __device__ __forceinline__ void derivs_tail(const DevSim& p, long long s, const 
             }
 }
 
+// i and i + 1 are opposite velocities for every odd i (the tables' order)
+template <int LAT>
+__host__ __device__ constexpr bool pairs_opposite()
+{
+    using L = Lat<LAT>;
+    for (int i = 1; i < L::Q; i += 2)
+        if (L::cx(i + 1) != -L::cx(i) || L::cy(i + 1) != -L::cy(i) || L::cz(i + 1) != -L::cz(i) ||
+            L::shell(i + 1) != L::shell(i))
+            return false;
+    return (L::Q & 1) == 1;
+}
+
 // Collision of one site with Sigma and Xi' known, and push streaming (S11, S12).
+// For a pair c, -c every term of n*_i is even or odd in c:
+//   n^eq   = w rho [1 + (c.u)/cs2 + (c.u)^2/(2 cs2^2) - u.u/(2 cs2)]   (Sec. III)
+//   Delta^int + Delta^corr = w(rho0) [cf_int c.f + cf_jt c.j~ + cf_h2 h2 + cf_h3 h3]
+//   h2 = Sigma : c c - cs0 tr Sigma,  h3 = Xi' : c c c - 3 cs0 (tr Xi')_b c_b     (Sec. VIII)
+// so the pair costs one evaluation of the even part E and the odd part O: n*_{+-} = E +- O.
 template <int LAT, typename T, int S, bool READ>
 __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Site& r, T drs, const T (&u)[3],
                                              const T (&f)[3], const T (&jtl)[3], const T (&Sig)[3][3],
@@ -632,6 +652,7 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
     using L = Lat<LAT>;
     using C = Codec<S>;
     constexpr int D = L::D;
+    static_assert(pairs_opposite<LAT>(), "velocity table must list opposite pairs");
     const long long s = r.s;
     const Phys<T>& q = phys<T>(p);
     const T rs = q.rho0 + drs;
@@ -641,32 +662,22 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
     T trS = T(0);
 #pragma unroll
     for (int a = 0; a < D; ++a) trS += Sig[a][a];
-    T trX[3];
+    const T ics2 = T(1) / cs2;
+    T uu = T(0);
+#pragma unroll
+    for (int a = 0; a < D; ++a) uu += u[a] * u[a];
+    const T g = q.gamma, omg = T(1) - g;
+    const T A1 = T(0.5) * ics2 * ics2, B1 = T(-0.5) * uu * ics2;
+    const T h2c = -cs0 * trS;  // the c-independent part of h2
+    // c.V gathers the odd terms linear in c: cf_int f + cf_jt j~ - 3 cs0 cf_h3 tr Xi'
+    T V[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int b = 0; b < D; ++b) {
         T t = T(0);
 #pragma unroll
         for (int a = 0; a < D; ++a) t += Xi[sym3<D>(a, a, b)];
-        trX[b] = t;
+        V[b] = q.cf_int * f[b] + q.cf_jt * jtl[b] - T(3) * cs0 * q.cf_h3 * t;
     }
-    const T ics2 = T(1) / cs2;
-    T uu = T(0);
-#pragma unroll
-    for (int a = 0; a < D; ++a) uu += u[a] * u[a];
-    T wl[L::NSHELL], w0[L::NSHELL], dw0[L::NSHELL];
-#pragma unroll
-    for (int k = 0; k < L::NSHELL; ++k) {
-        wl[k] = weight<LAT, T>(k, cs2);
-        w0[k] = q.w0[k];
-        // n^eq - w(rho0) rho0 = w rho X + w drho + rho0 (w(s) - w(s0)), and
-        // w(s) - w(s0) = (s - s0) [c1 + c2 (s + s0) + c3 (s^2 + s s0 + s0^2)]
-        dw0[k] = C::DEV ? wl[k] * drs + q.rho0 * dcs2 *
-                                           (T(Lat<LAT>::wc(k, 1)) + T(Lat<LAT>::wc(k, 2)) * (cs2 + cs0) +
-                                            T(Lat<LAT>::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0))
-                        : T(0);
-    }
-    const T g = q.gamma;
-    const T cf_int = q.cf_int, cf_jt = q.cf_jt, cf_h2 = q.cf_h2, cf_h3 = q.cf_h3;
     // wrapped destination offsets (site indices < 2^31) for the shifts -4, -2, -1, 0, 1, 2, 4
     // that the velocity components take
     int ox[7], oy[7], oz[7];
@@ -684,41 +695,63 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
     T stored_sum = T(0);
     float sh = 0.f, sl = 0.f;  // float-pair sum of the stored values (EXACT storages)
 #pragma unroll
-    for (int i = 1; i < L::Q; ++i) {
+    for (int i = 1; i < L::Q; i += 2) {
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const int c[3] = {cx, cy, cz};
         const int k = L::shell(i);
-        T uc = T(0), cf = T(0), cjt = T(0);
+        // shell constants (pure in k: shared by the shell's pairs)
+        const T wl = weight<LAT, T>(k, cs2);
+        const T wr = wl * rs;
+        const T w0k = q.w0[k];
+        T even0;
+        if (C::DEV) {
+            // n^eq - w(rho0) rho0 = w rho X + w drho + rho0 (w(s) - w(s0)), with
+            // w(s) - w(s0) = (s - s0) [c1 + c2 (s + s0) + c3 (s^2 + s s0 + s0^2)]
+            const T dw0 = wl * drs + q.rho0 * dcs2 *
+                                         (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) +
+                                          T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
+            even0 = omg * (wr * B1 + dw0) + w0k * q.cf_h2 * h2c;
+        } else {
+            even0 = omg * wr * (T(1) + B1) + w0k * q.cf_h2 * h2c;
+        }
+        // the pair's c-dependent parts
+        T uc = T(0), lin = T(0), h2 = T(0), h3 = T(0);
 #pragma unroll
         for (int a = 0; a < D; ++a)
-            if (c[a]) { uc += T(c[a]) * u[a]; cf += T(c[a]) * f[a]; cjt += T(c[a]) * jtl[a]; }
-        T h2 = -cs0 * trS, h3 = T(0);
+            if (c[a]) { uc += T(c[a]) * u[a]; lin += T(c[a]) * V[a]; }
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
-            for (int b = 0; b < D; ++b)
-                if (c[a] && c[b]) h2 += Sig[a][b] * T(c[a] * c[b]);
+            for (int b = a; b < D; ++b)
+                if (c[a] && c[b]) h2 += T((a == b ? 1 : 2) * c[a] * c[b]) * Sig[a][b];
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
-            for (int b = 0; b < D; ++b)
+            for (int b = a; b < D; ++b)
 #pragma unroll
-                for (int cc = 0; cc < D; ++cc)
-                    if (c[a] && c[b] && c[cc]) h3 += Xi[sym3<D>(a, b, cc)] * T(c[a] * c[b] * c[cc]);
-#pragma unroll
-        for (int b = 0; b < D; ++b)
-            if (c[b]) h3 -= T(3) * cs0 * trX[b] * T(c[b]);
-        const T X = uc * ics2 + T(0.5) * uc * uc * ics2 * ics2 - T(0.5) * uu * ics2;
-        // n^eq in the storage's convention: n^eq itself, or n^eq - w_i(rho0) rho0
-        const T neq = C::DEV ? wl[k] * rs * X + dw0[k] : wl[k] * rs * (T(1) + X);
-        const T dcorr = w0[k] * (cf_int * cf + cf_jt * cjt + cf_h2 * h2 + cf_h3 * h3);
-        // n* = gamma n + (1 - gamma) n^eq + Delta^int + Delta^corr; the offsets cancel in the deviation form
-        T nstar = (T(1) - g) * neq + dcorr;
-        if (READ) nstar += g * pop_raw<S, T>(p, src, i, s);
-        const long long dst = ox[sidx(cx)] + oy[sidx(cy)] + oz[sidx(cz)];
-        const T stored = pop_put<S, T>(p, src ^ 1, i, dst, nstar);
-        if (C::EXACT) acc2(sh, sl, float(stored));
-        else stored_sum += stored;
+                for (int e = b; e < D; ++e)
+                    if (c[a] && c[b] && c[e]) {
+                        const int mult = (a == b && b == e) ? 1 : (a == b || b == e) ? 3 : 6;
+                        h3 += T(mult * c[a] * c[b] * c[e]) * Xi[sym3<D>(a, b, e)];
+                    }
+        const T E = omg * wr * A1 * uc * uc + w0k * q.cf_h2 * h2 + even0;
+        const T O = omg * wr * ics2 * uc + w0k * (lin + q.cf_h3 * h3);
+        T np = E + O, nm = E - O;
+        if (READ) {
+            np += g * pop_raw<S, T>(p, src, i, s);
+            nm += g * pop_raw<S, T>(p, src, i + 1, s);
+        }
+        const long long dp = ox[sidx(cx)] + oy[sidx(cy)] + oz[sidx(cz)];
+        const long long dm = ox[sidx(-cx)] + oy[sidx(-cy)] + oz[sidx(-cz)];
+        const T sp = pop_put<S, T>(p, src ^ 1, i, dp, np);
+        const T sm = pop_put<S, T>(p, src ^ 1, i + 1, dm, nm);
+        if (C::EXACT) {
+            acc2(sh, sl, float(sp));
+            acc2(sh, sl, float(sm));
+        } else {
+            stored_sum += sp;
+            stored_sum += sm;
+        }
     }
     // rest population: the stored convention sums to rho - rho0 (deviations) or rho
     if (C::EXACT) {
@@ -1131,6 +1164,20 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
     }
 }
 
+// Ring of the collision kernel: the 5 planes of the derivative stencil and PF planes in flight.
+template <int D>
+struct CollidePlan {
+    static constexpr int PF = D == 3 ? 1 : 0;
+    static constexpr int R = D == 3 ? 5 + PF : 1;
+    __device__ static int slot(int z) { return D == 3 ? (z + 8 * R) % R : 0; }  // z >= -8
+    template <typename T>
+    __device__ static void planes(T* ring, int plane_elems, int z, const T* (&pl)[5])
+    {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) pl[k] = ring + slot(D == 3 ? z - 2 + k : 0) * plane_elems;
+    }
+};
+
 // S11 (rest) and S12 (tiled): A, B, C of every plane go to the ring (halo 2);
 // d_a A, d_g B_ag and d_a C_b at the tile's sites complete Sigma; collide_tail
 // then collides and streams.
@@ -1145,7 +1192,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
     constexpr int RX = TX + 4, RY = TY + 4, NP = 1 + AL::NB + D;  // A, B, C
     constexpr int HZ = D == 3 ? 2 : 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sr = reinterpret_cast<T*>(smem_raw);  // [NZR][NP][RY][RX]
+    T* sr = reinterpret_cast<T*>(smem_raw);  // [R][NP][RY][RX]
     const int tid = threadIdx.x, nth = blockDim.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
@@ -1165,37 +1212,38 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
         const int k = tid + m * nth;
         hoff[m] = k < RX * RY ? wrapm(x0 - 2 + k % RX, p.nx) + p.nx * wrapm(y0 - 2 + k / RX, p.ny) : 0;
     }
-    T pa[MR][NP];
+    // A, B, C of plane zl into its ring slot, asynchronously
     auto fetch = [&](int zl) {
         const long long base = D == 3 ? (long long)wrapc(zl, p.nz) * p.nx * p.ny : 0;
+        T* dst = sr + CollidePlan<D>::slot(zl) * NP * RY * RX;
 #pragma unroll
         for (int m = 0; m < MR; ++m) {
             const int k = tid + m * nth;
             if (k < RX * RY) {
                 const long long g = base + hoff[m];
 #pragma unroll
-                for (int c = 0; c < NP; ++c) pa[m][c] = aux[(AL::A + c) * p.N + g];
+                for (int c = 0; c < NP; ++c) cp_async<sizeof(T)>(dst + c * RY * RX + k, aux + (AL::A + c) * p.N + g);
             }
         }
     };
-    fetch(z0 - HZ);
+    constexpr int PF = CollidePlan<D>::PF;
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        fetch(z0 - HZ + k);
+        cp_async_commit();
+    }
     for (int zl = z0 - HZ; zl < z1 + HZ; ++zl) {
-        {
-            T* dst = sr + ring_slot<D>(zl) * NP * RY * RX;
-#pragma unroll
-            for (int m = 0; m < MR; ++m) {
-                const int k = tid + m * nth;
-                if (k < RX * RY)
-#pragma unroll
-                    for (int c = 0; c < NP; ++c) dst[c * RY * RX + k] = pa[m][c];
-            }
-            if (zl + 1 < z1 + HZ) fetch(zl + 1);
-        }        __syncthreads();
+        // the slot of plane zl + PF held plane zl + PF - R, last read before the previous
+        // step's closing barrier
+        if (zl + PF < z1 + HZ) fetch(zl + PF);
+        cp_async_commit();
+        cp_async_wait<PF>();
+        __syncthreads();
         const int zc = zl - HZ;
         if (zc >= z0 && zc < z1) {
             const int gz = D == 3 ? zc : 0;
             const T* pl[5];
-            ring_planes<D, T>(sr, NP * RY * RX, zc, pl);
+            CollidePlan<D>::planes(sr, NP * RY * RX, zc, pl);
             constexpr int PS = RY * RX;
             for (int k = tid; k < TX * TY; k += nth) {
                 const int ix = k % TX, iy = k / TX;
@@ -1418,7 +1466,7 @@ KernelTable make_table(bool read_pops)
     constexpr int D = Lat<LAT>::D;
     t.smem_sweep = SweepPlan<D, T, U>::BYTES;
     t.smem_derivs = size_t(TL::NZR) * 6 * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
-    t.smem_collide = size_t(TL::NZR) * (1 + AuxLayout<D>::NB + D) * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
+    t.smem_collide = size_t(CollidePlan<D>::R) * (1 + AuxLayout<D>::NB + D) * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
     cudaFuncSetAttribute(t.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_sweep));
     cudaFuncSetAttribute(t.derivs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_derivs));
     cudaFuncSetAttribute(t.collide, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_collide));
