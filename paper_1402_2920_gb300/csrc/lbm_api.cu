@@ -225,9 +225,11 @@ int add_step(lbm_sim* s, cudaGraph_t g, cudaGraphNode_t dep, int src, cudaGraphN
         void* a[] = {&dv, &src, &pair};
         LBM_CK(add_kernel(g, &n1, s->kt.moments, dim3(G), B, a, d0, nd0));
     }
+    const dim3 TG = tile_grid(s);
+    const int TB = s->kt.tile_threads;
     {
         void* a[] = {&dv, &pair};
-        LBM_CK(add_kernel(g, &n2, s->kt.force, dim3(G), B, a, &n1, 1));
+        LBM_CK(add_kernel(g, &n2, s->kt.force, TG, TB, a, &n1, 1, s->kt.smem_force));
     }
     {
         void* a[] = {&dv, &pair};
@@ -242,8 +244,6 @@ int add_step(lbm_sim* s, cudaGraph_t g, cudaGraphNode_t dep, int src, cudaGraphN
     cp.conditional.size = 1;
     LBM_CK(cudaGraphAddNode(&nc, g, &n3, nullptr, 1, &cp));
     cudaGraph_t body = cp.conditional.phGraph_out[0];
-    const dim3 TG = tile_grid(s);
-    const int TB = s->kt.tile_threads;
     {
         cudaGraphNode_t b1, b3;
         void* a1[] = {&dv, &pair};
@@ -361,7 +361,7 @@ int run_fields(lbm_sim* s)
     const int B = s->kt.block, G = nblocks(dv.N, B);
     const int pair = 1;
     LBM_CK(launch(s, s->kt.moments, G, B, dv, s->cur, pair));
-    LBM_CK(launch(s, s->kt.force, G, B, dv, pair));
+    LBM_CK(launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair));
     LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
     cudaGraphConditionalHandle h{};
     const int no = 0;
@@ -640,7 +640,7 @@ int step_direct(lbm_sim* s)
     const int pair = 0, no = 0, src = s->cur;
     cudaGraphConditionalHandle h{};
     LBM_CK(launch(s, s->kt.moments, G, B, dv, src, pair));
-    LBM_CK(launch(s, s->kt.force, G, B, dv, pair));
+    LBM_CK(launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair));
     LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
     for (int it = 0; it < dv.maxit + 1; ++it) {
         LBM_CK(launch_tiled(s, s->kt.sweep, s->kt.smem_sweep, dv, pair));
@@ -816,7 +816,7 @@ int lbm_profile(lbm_sim* s, int reps, double* ms_out, int n)
     LBM_CK(cudaEventCreate(&e1));
     // the scratch u-solve pair; the collision writes the spare population buffer
     LBM_CK(launch(s, s->kt.moments, G, B, dv, src, pair));
-    LBM_CK(launch(s, s->kt.force, G, B, dv, pair));
+    LBM_CK(launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair));
     LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
     int rc = LBM_OK;
     for (int k = 0; k < 5 && rc == LBM_OK; ++k) {
@@ -825,7 +825,7 @@ int lbm_profile(lbm_sim* s, int reps, double* ms_out, int n)
             cudaError_t e = cudaSuccess;
             switch (k) {
             case 0: e = launch(s, s->kt.moments, G, B, dv, src, pair); break;
-            case 1: e = launch(s, s->kt.force, G, B, dv, pair); break;
+            case 1: e = launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair); break;
             case 2: e = launch_tiled(s, s->kt.sweep, s->kt.smem_sweep, dv, pair); break;
             case 3: e = launch_tiled(s, s->kt.derivs, s->kt.smem_derivs, dv); break;
             case 4: e = launch_tiled(s, s->kt.collide, s->kt.smem_collide, dv, src); break;

@@ -117,7 +117,7 @@ struct KernelTable {
     int block;                // threads per block of the per-site kernels
     int tile[3];              // TX, TY, ZB of the tiled kernels
     int tile_threads;
-    size_t smem_sweep, smem_derivs, smem_collide;  // dynamic shared memory bytes
+    size_t smem_force, smem_sweep, smem_derivs, smem_collide;  // dynamic shared memory bytes
     size_t tsize, usize, ssize;  // bytes of T, U and the storage type
     size_t rsize;                // bytes of a rest-plane element (0: no separate plane)
     bool exact;                  // FP64 density bookkeeping (rho_lo is used)

@@ -428,51 +428,6 @@ __global__ void __launch_bounds__(256, 3) k_moments(DevSim p, int src, int pair)
 }
 
 // ---------------------------------------------------------------------------
-// S2: interface force (Sec. VI with the third-derivative stencil of Sec. IV.E)
-// ---------------------------------------------------------------------------
-template <int LAT, typename T, typename U>
-__global__ void k_force(DevSim p, int pair)
-{
-    using L = Lat<LAT>;
-    const long long s = gtid();
-    if (s >= p.N) return;
-    const Site r = site_of(p, s);
-    const T* drho = cp<T>(p.rho);
-    auto R = [&](int dx, int dy, int dz) { return drho[shifted(p, r, dx, dy, dz)]; };  // rho - rho0
-    T f[3];
-#pragma unroll
-    for (int a = 0; a < L::D; ++a) {
-        const int ex = a == 0, ey = a == 1, ez = a == 2;
-        const T ax = R(ex, ey, ez) - R(-ex, -ey, -ez);
-        const T two = R(2 * ex, 2 * ey, 2 * ez) - R(-2 * ex, -2 * ey, -2 * ez);
-        T diag = T(0);
-#pragma unroll
-        for (int b = 0; b < L::D; ++b) {
-            if (b == a) continue;
-            const int bx = b == 0, by = b == 1, bz = b == 2;
-#pragma unroll
-            for (int sg = -1; sg <= 1; sg += 2)
-                diag += R(ex + sg * bx, ey + sg * by, ez + sg * bz) - R(-ex + sg * bx, -ey + sg * by, -ez + sg * bz);
-        }
-        // sum_i tau_i d_ia rho(r + d_i): the (2 0) shell has d_a = +-2
-        const T lap3 = T(L::T3_AX) * ax + T(L::T3_DIAG) * diag + T(2.0 * L::T3_TWO) * two;
-        f[a] = phys<T>(p).kappa * (phys<T>(p).rho0 + drho[s]) * lap3;
-    }
-    // S2: j0' = j0 + (h/2) f; S3 for the start of the u-solve: u = (j0' + j~)/rho with j~ of the
-    // previous step (warm start, Sec. IX item 3) or j~ = 0 (S1)
-    const U rho = phys<U>(p).rho0 + U(drho[s]);
-    const U* jw = cp<U>(p.jt_warm);
-    U* u0 = mp<U>(p.uit[pair][p.us[pair].cur]);
-#pragma unroll
-    for (int a = 0; a < L::D; ++a) {
-        mp<T>(p.f)[a * p.N + s] = f[a];
-        const T j = mp<T>(p.j0p)[a * p.N + s] + T(0.5) * f[a];
-        mp<T>(p.j0p)[a * p.N + s] = j;
-        u0[a * p.N + s] = (U(j) + (p.warm ? jw[a * p.N + s] : U(0))) / rho;
-    }
-}
-
-// ---------------------------------------------------------------------------
 // S3-S7: the implicit u-solve (Sec. IX)
 // ---------------------------------------------------------------------------
 // Frozen-coefficient largest eigenvalue of the iteration at density rho:
@@ -808,6 +763,13 @@ __device__ __forceinline__ void ring_planes(T* ring, int plane_elems, int z, con
 
 // First derivative of Sec. IV.B along axis a, (2/3)(g(+1) - g(-1)) - (1/12)(g(+2) - g(-2)),
 // of a field read by g(plane, index) at in-plane index i (row pitch PX) of the centre plane.
+// The Sec. IV.B first derivative from the values at offsets -2, -1, +1, +2.
+template <typename T>
+__device__ __forceinline__ T d1v(T m2, T m1, T p1, T p2)
+{
+    return T(2.0 / 3.0) * (p1 - m1) - T(1.0 / 12.0) * (p2 - m2);
+}
+
 template <typename T, class G>
 __device__ __forceinline__ T d1p(const T* const (&pl)[5], int a, int i, int PX, G g)
 {
@@ -831,6 +793,31 @@ __device__ __forceinline__ void cp_async(void* sdst, const void* gsrc)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Two consecutive shared-memory elements in one access (the index must be even).
+template <typename U>
+struct Vec2;
+template <>
+struct Vec2<float> {
+    using type = float2;
+};
+template <>
+struct Vec2<double> {
+    using type = double2;
+};
+template <typename U>
+__device__ __forceinline__ typename Vec2<U>::type ld2(const U* p)
+{
+    return *reinterpret_cast<const typename Vec2<U>::type*>(p);
+}
+template <typename U>
+__device__ __forceinline__ void st2(U* p, U a, U b)
+{
+    typename Vec2<U>::type v;
+    v.x = a;
+    v.y = b;
+    *reinterpret_cast<typename Vec2<U>::type*>(p) = v;
+}
 
 // Shared-memory plan of the sweep: a ring of R planes of u (sweep precision) and rho - rho0
 // (storage precision) with in-plane halo 4, PF of them in flight, and the q planes, which
@@ -867,6 +854,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2
     constexpr int D = L::D;
     using TL = Tile<D>;
     using SP = SweepPlan<D, T, U>;
+    using V2 = typename Vec2<U>::type;
     constexpr int TX = TL::TX, TY = TL::TY, NT = TL::THREADS;
     constexpr int UX = SP::UX, UP = SP::UP, QX = SP::QX, QY = SP::QY, QP = SP::QP, NQ = SP::NQ;
     constexpr int PF = SP::PF, R = SP::R;
@@ -965,30 +953,51 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2
         const int zq = zl - HZ / 2;
         const bool qplane = D == 2 || (zq >= z0 - 2 && zq < z1 + 2);
         U* qb = sq + (D == 3 ? (zq & 1) : 0) * NQ * QP;
-        if (qplane) {  // stage Q: plane zq
+        if (qplane) {  // stage Q: plane zq, two x-neighbouring points per thread (64-bit reads)
             const U* pl[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) pl[k] = su + slot(D == 3 ? zq - 2 + k : 0) * D * UP;
             const T* rq = sr + slot(zq) * UP;
-            for (int k = tid; k < QY * UX; k += NT) {
-                if (k % UX >= QX) continue;
-                const int ui = k + 2 * UX + 2;  // (qy + 2) UX + qx + 2
-                U du[3][3];
+            constexpr int PX = UX / 2;  // point pairs per row of the pitch
+            for (int t = tid; t < QY * PX; t += NT) {
+                const int qx = 2 * (t % PX), qy = t / PX;
+                if (qx >= QX) continue;
+                const int k = qy * UX + qx;      // even: the pair is 2-element aligned
+                const int ui = k + 2 * UX + 2;   // (qy + 2) UX + qx + 2
+                U du[2][3][3];                   // [point][a][b] = d_a u_b
 #pragma unroll
-                for (int b = 0; b < D; ++b)
+                for (int b = 0; b < D; ++b) {
+                    const U* P = pl[2] + b * UP;
+                    const V2 xm = ld2<U>(P + ui - 2), xc = ld2<U>(P + ui), xp = ld2<U>(P + ui + 2);
+                    du[0][0][b] = d1v<U>(xm.x, xm.y, xc.y, xp.x);
+                    du[1][0][b] = d1v<U>(xm.y, xc.x, xp.x, xp.y);
+                    const V2 ym2 = ld2<U>(P + ui - 2 * UX), ym1 = ld2<U>(P + ui - UX);
+                    const V2 yp1 = ld2<U>(P + ui + UX), yp2 = ld2<U>(P + ui + 2 * UX);
+                    du[0][1][b] = d1v<U>(ym2.x, ym1.x, yp1.x, yp2.x);
+                    du[1][1][b] = d1v<U>(ym2.y, ym1.y, yp1.y, yp2.y);
+                    if (D == 3) {
+                        const V2 zm2 = ld2<U>(pl[0] + b * UP + ui), zm1 = ld2<U>(pl[1] + b * UP + ui);
+                        const V2 zp1 = ld2<U>(pl[3] + b * UP + ui), zp2 = ld2<U>(pl[4] + b * UP + ui);
+                        du[0][2][b] = d1v<U>(zm2.x, zm1.x, zp1.x, zp2.x);
+                        du[1][2][b] = d1v<U>(zm2.y, zm1.y, zp1.y, zp2.y);
+                    }
+                }
+                U qv[2][NQ];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    U P, DP, PM, RPP;
+                    eos_full<U>(p, phys<U>(p).rho0 + U(rq[ui + h]), P, DP, PM, RPP);
+                    U div = U(0);
+#pragma unroll
+                    for (int a = 0; a < D; ++a) div += du[h][a][a];
 #pragma unroll
                     for (int a = 0; a < D; ++a)
-                        du[a][b] = d1p<U>(pl, a, ui, UX, [&](const U* P, int j) { return P[b * UP + j]; });
-                U P, DP, PM, RPP;
-                eos_full<U>(p, phys<U>(p).rho0 + U(rq[ui]), P, DP, PM, RPP);
-                U div = U(0);
 #pragma unroll
-                for (int a = 0; a < D; ++a) div += du[a][a];
+                        for (int b = a; b < D; ++b)
+                            qv[h][sym2<D>(a, b)] = (a == b ? PM * div : U(0)) + P * (du[h][b][a] + du[h][a][b]);
+                }
 #pragma unroll
-                for (int a = 0; a < D; ++a)
-#pragma unroll
-                    for (int b = a; b < D; ++b)
-                        qb[sym2<D>(a, b) * QP + k] = (a == b ? PM * div : U(0)) + P * (du[b][a] + du[a][b]);
+                for (int c = 0; c < NQ; ++c) st2<U>(qb + c * QP + k, qv[0][c], qv[1][c]);
             }
         }
         __syncthreads();
@@ -1057,6 +1066,127 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2
     // NaN -> +inf, which orders above every finite residual
     const double dmax_d = bad ? __longlong_as_double(0x7ff0000000000000ll) : double(dmax);
     block_max2(dmax_d, double(jmax), &p.us[pair].resid_bits, &p.us[pair].jmax_bits);
+}
+
+// S2 (tiled): f = kappa rho d_a lap rho with the third-derivative stencil of Sec. IV.E,
+// j0' = j0 + (h/2) f, and the start of the u-solve u = (j0' + j~)/rho with j~ of the previous
+// step (warm start, Sec. IX item 3) or j~ = 0 (S1).  The CTA marches along z; rho - rho0 of
+// each plane (in-plane halo 2) arrives by cp.async in a ring of 5 + PF planes.
+template <int D>
+struct ForcePlan {
+    using TL = Tile<D>;
+    static constexpr int RX = TL::TX + 4, RY = TL::TY + 4, RP = RX * RY;
+    static constexpr int PF = D == 3 ? 2 : 0;
+    static constexpr int R = D == 3 ? 5 + PF : 1;
+    __device__ static int slot(int z) { return D == 3 ? (z + 8 * R) % R : 0; }  // z >= -8
+};
+
+template <int LAT, typename T, typename U>
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_force(DevSim p, int pair)
+{
+    using L = Lat<LAT>;
+    constexpr int D = L::D;
+    using TL = Tile<D>;
+    using FP = ForcePlan<D>;
+    constexpr int TX = TL::TX, TY = TL::TY, NT = TL::THREADS;
+    constexpr int RX = FP::RX, RP = FP::RP, PF = FP::PF;
+    constexpr int HZ = D == 3 ? 2 : 0;
+    static_assert(TX * TY == NT, "one site per thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sr = reinterpret_cast<T*>(smem_raw);  // [R][RY][RX]: rho - rho0
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
+    const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
+    const long long NP = (long long)p.nx * p.ny;
+    const T* drho = cp<T>(p.rho);
+    T* j0p = mp<T>(p.j0p);
+    T* fo = mp<T>(p.f);
+    const U* jw = cp<U>(p.jt_warm);
+    U* u0 = mp<U>(p.uit[pair][p.us[pair].cur]);
+    const int ix = tid % TX, iy = tid / TX;
+    const int gx = x0 + ix, gy = y0 + iy;
+    const bool own = gx < p.nx && gy < p.ny;
+    const long long own_xy = (long long)gy * p.nx + gx;
+    constexpr int MR = (RP + NT - 1) / NT;
+    int hoff[MR];  // wrapped in-plane offsets of the halo points
+#pragma unroll
+    for (int m = 0; m < MR; ++m) {
+        const int k = tid + m * NT;
+        hoff[m] = k < RP ? wrapm(x0 - 2 + k % RX, p.nx) + p.nx * wrapm(y0 - 2 + k / RX, p.ny) : 0;
+    }
+    auto fetch = [&](int zl) {
+        const long long base = D == 3 ? (long long)wrapc(zl, p.nz) * NP : 0;
+        T* dst = sr + FP::slot(zl) * RP;
+#pragma unroll
+        for (int m = 0; m < MR; ++m) {
+            const int k = tid + m * NT;
+            if (k < RP) cp_async<sizeof(T)>(dst + k, drho + base + hoff[m]);
+        }
+    };
+    // own-site inputs (j0, warm-start j~), fetched one plane ahead
+    T pj[3] = {T(0), T(0), T(0)};
+    U pw[3] = {U(0), U(0), U(0)};
+    auto fetch_own = [&](int z) {
+        if (own && z >= z0 && z < z1) {
+            const long long g = (D == 3 ? z * NP : 0) + own_xy;
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                pj[a] = j0p[a * p.N + g];
+                pw[a] = p.warm ? jw[a * p.N + g] : U(0);
+            }
+        }
+    };
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        fetch(z0 - HZ + k);
+        cp_async_commit();
+    }
+    fetch_own(z0);
+    for (int zl = z0 - HZ; zl < z1 + HZ; ++zl) {
+        // the slot of plane zl + PF held plane zl + PF - R, last read before the previous
+        // step's closing barrier
+        if (zl + PF < z1 + HZ) fetch(zl + PF);
+        cp_async_commit();
+        cp_async_wait<PF>();
+        __syncthreads();
+        const int zc = zl - HZ;
+        if (own && zc >= z0 && zc < z1) {
+            const T* pl[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) pl[k] = sr + FP::slot(D == 3 ? zc - 2 + k : 0) * RP;
+            const int ri = (iy + 2) * RX + ix + 2;
+            // rho - rho0 at offset (dx, dy, dz) from the site
+            auto R = [&](int dx, int dy, int dz) { return pl[2 + dz][ri + dx + dy * RX]; };
+            const long long g = (D == 3 ? zc * NP : 0) + own_xy;
+            const T rs = phys<T>(p).rho0 + R(0, 0, 0);
+            const U rho = U(rs);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                const int ex = a == 0, ey = a == 1, ez = a == 2;
+                const T ax = R(ex, ey, ez) - R(-ex, -ey, -ez);
+                const T two = R(2 * ex, 2 * ey, 2 * ez) - R(-2 * ex, -2 * ey, -2 * ez);
+                T diag = T(0);
+#pragma unroll
+                for (int b = 0; b < D; ++b) {
+                    if (b == a) continue;
+                    const int bx = b == 0, by = b == 1, bz = b == 2;
+#pragma unroll
+                    for (int sg = -1; sg <= 1; sg += 2)
+                        diag += R(ex + sg * bx, ey + sg * by, ez + sg * bz) - R(-ex + sg * bx, -ey + sg * by, -ez + sg * bz);
+                }
+                // sum_i tau_i d_ia rho(r + d_i): the (2 0) shell has d_a = +-2
+                const T lap3 = T(L::T3_AX) * ax + T(L::T3_DIAG) * diag + T(2.0 * L::T3_TWO) * two;
+                const T fa = phys<T>(p).kappa * rs * lap3;
+                const T j = pj[a] + T(0.5) * fa;  // S2: j0' = j0 + (h/2) f
+                fo[a * p.N + g] = fa;
+                j0p[a * p.N + g] = j;
+                u0[a * p.N + g] = (U(j) + pw[a]) / rho;
+            }
+        }
+        if (zc >= z0 && zc < z1) fetch_own(zc + 1);
+        __syncthreads();
+    }
 }
 
 // S8 and S10 (tiled): the pointwise rho, u, p of every plane go to the ring
@@ -1465,8 +1595,10 @@ KernelTable make_table(bool read_pops)
     t.tile_threads = TL::THREADS;
     constexpr int D = Lat<LAT>::D;
     t.smem_sweep = SweepPlan<D, T, U>::BYTES;
+    t.smem_force = size_t(ForcePlan<D>::R) * ForcePlan<D>::RP * sizeof(T);
     t.smem_derivs = size_t(TL::NZR) * 6 * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
     t.smem_collide = size_t(CollidePlan<D>::R) * (1 + AuxLayout<D>::NB + D) * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
+    cudaFuncSetAttribute(t.force, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_force));
     cudaFuncSetAttribute(t.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_sweep));
     cudaFuncSetAttribute(t.derivs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_derivs));
     cudaFuncSetAttribute(t.collide, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_collide));
