@@ -214,7 +214,8 @@ def run_native(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     P.load_library()
 
-    case = W.make_case("spinodal3d")
+    n = args.side
+    case = W.make_case("spinodal3d", dims=(n, n, n))
     storage = STORAGES[args.storage]
     a, b, T = case.eos_abT
     stream = torch.cuda.current_stream()
@@ -275,7 +276,7 @@ def run_native(args):
     achieved = alg[dom] * N / (prof[dom] / 1e3) / 1e9
     step_gbs = 2 * 59 * sb * N / (ms / K / 1e3) / 1e9  # whole step against 2 Q s bytes per site
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": _traffic(dom, "spinodal3d_256"), "kernel": dom,
+                "traffic": _traffic(dom, "spinodal3d_%d" % n), "kernel": dom,
                 "algorithmic_bytes_per_site": alg[dom], "peak_source": peak_kind,
                 "step": {"algorithmic_bytes_per_site": 2 * 59 * sb, "achieved": step_gbs,
                          "frac": step_gbs / peak}}
@@ -322,12 +323,12 @@ def run_native(args):
         line = {"metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
                 "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.storage in ("f32", "f32dev") else args.storage, "data": "synthetic",
-                "config": {"workload": "D3Q59 256^3 periodic spinodal (rho = 1 +- 1%% of noise, seed 0), vdW T/Tc=%g, "
-                                       "kappa=%.5f, gamma=0" % (case.Tr, case.kappa),
+                "config": {"workload": "D3Q59 %d^3 periodic spinodal (rho = 1 +- 1%% of noise, seed 0), vdW T/Tc=%g, "
+                                       "kappa=%.5f, gamma=0" % (n, case.Tr, case.kappa),
                            "storage": {"f32": "FP32 populations", "f32dev": "FP32 deviations n_i - w_i(rho0) rho0",
                                        "f16dev": "FP16 deviations", "bf16dev": "BF16 deviations"}[args.storage],
                            "usolve": "FP32 sweeps, Chebyshev-accelerated for the spectrum [0, g], |dj~| <= 5e-9",
-                           "parallelism": "replicas x%d" % ws, "l2": "inputs (populations 7.9 GB) larger than L2",
+                           "parallelism": "replicas x%d" % ws, "l2": "inputs (populations %.1f GB) larger than L2" % (2 * 59 * STORAGE_BYTES[args.storage] * N / 2 / 1e9),
                            "sites": N},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches, "usolve_sweeps_per_step": sweeps / K,
@@ -349,6 +350,8 @@ def main():
     ap.add_argument("--storage", choices=sorted(STORAGES), default="f32dev")
     ap.add_argument("--ref-side", type=int, default=48)
     ap.add_argument("--no-extras", action="store_true")
+    # the benchmark workload is the 256^3 cube; smaller cubes of the same recipe serve profiling
+    ap.add_argument("--side", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
