@@ -193,6 +193,29 @@ int lbm_step_batch(lbm_sim* const* sims, int n, const int64_t* nsteps);
 /* Static description of an error code. */
 const char* lbm_error_string(int code);
 
+/* Mass and momentum of a population array, computed without allocating anything.
+ *   The sums are those lbm_stats_get reports, rho = sum_i n_i and j = sum_i n_i c_i
+ *   over all sites (Sec. II).  The paper has no counterpart of the no-allocation form:
+ *   it exists for callers that may not use the device allocator, such as a serving
+ *   loop that has handed its whole memory budget to admitted simulations, or a monitor
+ *   of running simulations that must not synchronise the device.
+ *   lattice: LBM_D2Q21 or LBM_D3Q59.  pops: device pointer to FP64 populations
+ *   [Q][n_sites], in the velocity order of lbm_velocities (the layout lbm_populations
+ *   writes).  n_sites: 1 .. 67,108,864 (= 4096 blocks x 256 threads x 64 sites, the
+ *   capacity of the library's fixed scratch array); larger counts return
+ *   LBM_E_INVALID_ARG and launch nothing.  sums: device pointer to 4 doubles that
+ *   receive (mass, j_x, j_y, j_z); j_z = 0 in 2D.  cuda_stream: the stream the two
+ *   kernels run on (NULL: legacy default stream); the call does not synchronise.
+ *   Caller memory is borrowed for the duration of the kernels.
+ *   Scratch: one 128 KB device array per device, shared by all calls; its address is
+ *   looked up (cudaGetSymbolAddress) on the first call made on each device, with that
+ *   device current, so make that first call before any stream capture starts.  Nothing
+ *   in the scratch must start at zero.  Calls on one device whose kernels may overlap
+ *   (different streams, or host threads) race on the scratch; calls ordered on one
+ *   stream do not.  Errors: LBM_E_INVALID_ARG (lattice, NULL pointer, n_sites out of
+ *   range), LBM_E_CUDA (no device, launch failure). */
+int lbm_moment_sums_noalloc(int lattice, const double* pops, int64_t n_sites, double* sums, void* cuda_stream);
+
 /* Free a simulation and its device memory.  NULL is accepted. */
 void lbm_destroy(lbm_sim* sim);
 

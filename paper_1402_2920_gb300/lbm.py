@@ -25,7 +25,7 @@ LBM_E_OOM, LBM_E_CUDA, LBM_E_TIMEOUT, LBM_E_IO = -5, -6, -7, -8
 #: every entry point the header declares (checked against the library's exports by the tests)
 ENTRY_POINTS = ("lbm_create", "lbm_footprint_bytes", "lbm_init", "lbm_step", "lbm_fields", "lbm_populations",
                 "lbm_set_populations", "lbm_velocities", "lbm_stats_get", "lbm_sync", "lbm_save", "lbm_load",
-                "lbm_step_batch", "lbm_error_string", "lbm_destroy", "lbm_profile")
+                "lbm_step_batch", "lbm_error_string", "lbm_destroy", "lbm_profile", "lbm_moment_sums_noalloc")
 
 #: kernel order of lbm_profile
 PROFILE_STAGES = ("moments", "force", "usolve_sweep", "derivs", "collide")
@@ -209,6 +209,18 @@ def lbm_save(sim, path):
 
 def lbm_load(sim, path):
     _check(load_library().lbm_load(ctypes.c_void_p(sim), os.fsencode(path)), "lbm_load")
+
+
+def lbm_moment_sums_noalloc(lattice, pops, n_sites, sums, stream=None):
+    """(mass, j_x, j_y, j_z) of FP64 device populations [Q][n_sites] into the 4-element
+    device tensor `sums`, on `stream`, without any allocation (does not synchronise)."""
+    def addr(a):
+        return a.data_ptr() if hasattr(a, "data_ptr") else int(a)
+
+    rc = load_library().lbm_moment_sums_noalloc(int(lattice), ctypes.c_void_p(addr(pops)), ctypes.c_int64(n_sites),
+                                                ctypes.c_void_p(addr(sums)),
+                                                ctypes.c_void_p(int(stream) if stream else 0))
+    _check(rc, "lbm_moment_sums_noalloc")
 
 
 def lbm_profile(sim, reps=10):
