@@ -112,7 +112,9 @@ def _algorithmic_bytes(lattice, storage_bytes, read_pops, chebyshev=True):
 def _kernel_sources_sha():
     h = hashlib.sha256()
     cdir = os.path.join(ROOT, "paper_1402_2920_gb300", "csrc")
-    for name in sorted(os.listdir(cdir)):
+    for name in sorted(os.listdir(cdir)):  # the files that define the kernels
+        if not (name.startswith("kernels_") or name in ("lbm_kernels.cuh", "lbm_lattice.h", "lbm_common.h")):
+            continue
         with open(os.path.join(cdir, name), "rb") as fh:
             h.update(name.encode())
             h.update(fh.read())
@@ -315,6 +317,19 @@ def run_native(args):
            "d2h_bytes_per_step": 4 * N * 8 / K,
            "definition": "lbm_init from pinned host rho, %d steps, lbm_fields (S1-S8) back to pinned host" % K}
 
+    # serving: continuous batching of the seeded droplet request stream at 0.8 of the measured
+    # batched throughput; latency from arrival to the result in host memory
+    serving = None
+    if args.serving_requests > 0 and not args.no_extras:
+        del sim
+        torch.cuda.empty_cache()
+        from paper_1402_2920_gb300 import serving as S
+
+        st, _, _ = S.run(n=args.serving_requests, load=0.8, calibrate=min(24, args.serving_requests))
+        serving = dict(st, unit="s", workload="first %d requests of the seed-1 stream (droplets, D2Q21 64^2-512^2 "
+                                               "and D3Q59 32^3-128^3, 500-5000 steps, FP32 deviations)"
+                       % args.serving_requests)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_extras:
         cpu = _cpu_baseline()
@@ -332,7 +347,7 @@ def run_native(args):
                            "sites": N},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches, "usolve_sweeps_per_step": sweeps / K,
-                "kernel_ms": prof}
+                "kernel_ms": prof, "serving": serving}
         line.update(extra)
         print(json.dumps(line), flush=True)
     if dist:
@@ -352,6 +367,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     # the benchmark workload is the 256^3 cube; smaller cubes of the same recipe serve profiling
     ap.add_argument("--side", type=int, default=256)
+    # requests of the serving stream to replay (256 is the whole stream; 0 skips it)
+    ap.add_argument("--serving-requests", type=int, default=32)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

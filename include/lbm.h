@@ -190,6 +190,51 @@ int lbm_load(lbm_sim* sim, const char* path);
  * as when that simulation is stepped alone. */
 int lbm_step_batch(lbm_sim* const* sims, int n, const int64_t* nsteps);
 
+/* ---------------------------------------------------------------------------
+ * Serving: many independent simulations of mixed lattice and size, admitted as they
+ * arrive (no counterpart in the paper; the physics of each request is lbm_step's).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int lattice;            /* LBM_D2Q21 or LBM_D3Q59                                  */
+    int64_t dims[3];        /* as for lbm_create                                       */
+    lbm_eos eos;
+    lbm_params params;
+    int64_t steps;          /* time steps to run (>= 0)                                */
+    double arrival_s;       /* arrival time in seconds after lbm_serve starts (>= 0)   */
+    const double* rho_init; /* host, N doubles [z][y][x]: initial density (required)   */
+    const double* u_init;   /* host, d*N doubles or NULL (u = 0)                       */
+    double* rho_out;        /* host, N doubles or NULL: rho after the last step (S1)   */
+    double* u_out;          /* host, d*N doubles or NULL: u after the last step (S8)   */
+} lbm_request;
+
+typedef struct {
+    double admit_s;         /* when the request got its slot (-1: never admitted)      */
+    double finish_s;        /* when its result was in the host buffers                 */
+    int status;             /* LBM_OK or the request's own error code                  */
+    int64_t steps_done;
+    size_t footprint;       /* device bytes it was admitted with                       */
+} lbm_request_result;
+
+typedef struct {
+    size_t memory_budget;   /* device bytes for simulations; 0: 90 % of free memory     */
+    int max_active;         /* simulations resident at once (one stream each)           */
+    int chunk_steps;        /* steps issued to a simulation per turn of the loop        */
+} lbm_serve_config;
+
+/* Run a stream of requests to completion on the current device (continuous batching).
+ *   A request is admitted once it has arrived, a slot is free and its footprint
+ *   (lbm_footprint_bytes) fits in the budget beside the running ones, in arrival order.
+ *   Admitted simulations stay resident and advance chunk_steps at a time on their own
+ *   streams, so their work overlaps on the device; finished ones hand their fields to
+ *   rho_out / u_out, free their slot and memory, and the next arrivals take them.  Each
+ *   result equals that of the same simulation stepped alone.  Blocks until every
+ *   request is done; per-request times and statuses go to out[n].  A request that can
+ *   never fit gets LBM_E_OOM, an invalid one LBM_E_INVALID_ARG; neither stops the
+ *   others.  Returns LBM_E_INVALID_ARG for bad arguments, LBM_E_CUDA when streams or
+ *   events cannot be made, LBM_OK otherwise.  Caller buffers are borrowed until the
+ *   call returns. */
+int lbm_serve(const lbm_request* reqs, int n, const lbm_serve_config* cfg, lbm_request_result* out);
+
 /* Static description of an error code. */
 const char* lbm_error_string(int code);
 

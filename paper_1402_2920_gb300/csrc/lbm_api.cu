@@ -177,7 +177,9 @@ size_t bytes_per_site(int lattice, int storage, size_t* ssize_out = nullptr)
     if (ssize_out) *ssize_out = ssize;
     const size_t usize = 8;  // worst case: FP64 u-solve
     const size_t rest = storage == LBM_STORE_F64 ? 0 : 2 * 8 + 4;  // two float-pair rest planes, rho_lo
-    return 2 * Q * ssize + rest + tsize * (1 + 3 + 3 + naux) + usize * (4 * 3 + 6);
+    // populations (two buffers), rest planes, rho - rho0, j0', f, aux; u iterates (2 x 2),
+    // warm-start j~ and the two Chebyshev update vectors
+    return 2 * Q * ssize + rest + tsize * (1 + 3 + 3 + naux) + usize * (4 * 3 + 3 + 2 * 3);
 }
 
 int validate(int lattice, const int64_t dims[3], int storage)
@@ -282,9 +284,12 @@ int build_graphs(lbm_sim* s)
     return LBM_OK;
 }
 
+// Device buffers come from the stream-ordered allocator on the simulation's stream:
+// creating and destroying simulations (a serving loop does it per request) then
+// neither synchronises the device nor stalls the other simulations' streams.
 int dev_alloc(lbm_sim* s, void** p, size_t bytes)
 {
-    cudaError_t e = cudaMalloc(p, bytes);
+    cudaError_t e = cudaMallocAsync(p, bytes, s->stream);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         *p = nullptr;
@@ -431,7 +436,8 @@ void lbm_destroy(lbm_sim* s)
         if (s->two[k].x) cudaGraphExecDestroy(s->two[k].x);
         if (s->two[k].g) cudaGraphDestroy(s->two[k].g);
     }
-    for (void* p : s->allocs) cudaFree(p);
+    for (void* p : s->allocs) cudaFreeAsync(p, s->stream);
+    if (s->stream) cudaStreamSynchronize(s->stream);
     (void)cudaGetLastError();
     delete s;
 }
@@ -557,7 +563,6 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
     for (int pr = 0; pr < 2; ++pr)
         for (int b = 0; b < 2; ++b) rc = rc ? rc : dev_alloc(s, &dv.uit[pr][b], 3 * N * U);
     rc = rc ? rc : dev_alloc(s, &dv.jt_warm, 3 * N * U);
-    rc = rc ? rc : dev_alloc(s, &dv.q, 6 * N * U);
     if (dv.cheb) {
         rc = rc ? rc : dev_alloc(s, &dv.dvec[0], 3 * N * U);
         rc = rc ? rc : dev_alloc(s, &dv.dvec[1], 3 * N * U);

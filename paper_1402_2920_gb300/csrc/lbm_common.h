@@ -74,7 +74,6 @@ struct DevSim {
     void* uit[2][2];      // U [3][N]: u iterates of the u-solve, ping-pong, for pair 0 (the run)
                           // and pair 1 (lbm_fields); u = (j0' + j~)/rho (S3)
     void* jt_warm;        // U [3][N]: j~ = rho u - j0' of the last step, the warm start (Sec. IX)
-    void* q;              // U [6][N]: symmetric q_ab of the u-solve (S4)
     void* aux;            // T [26][N]: A, B_ab, C_a, the local part of Sigma_ab, Xi'_abc
     UsolveState* us;      // [2]: pair 0 and pair 1
     unsigned* range;      // [2][2][kRangeSlots]: float bits of min and max density per pair

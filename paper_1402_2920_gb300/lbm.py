@@ -25,7 +25,8 @@ LBM_E_OOM, LBM_E_CUDA, LBM_E_TIMEOUT, LBM_E_IO = -5, -6, -7, -8
 #: every entry point the header declares (checked against the library's exports by the tests)
 ENTRY_POINTS = ("lbm_create", "lbm_footprint_bytes", "lbm_init", "lbm_step", "lbm_fields", "lbm_populations",
                 "lbm_set_populations", "lbm_velocities", "lbm_stats_get", "lbm_sync", "lbm_save", "lbm_load",
-                "lbm_step_batch", "lbm_error_string", "lbm_destroy", "lbm_profile", "lbm_moment_sums_noalloc")
+                "lbm_step_batch", "lbm_error_string", "lbm_destroy", "lbm_profile", "lbm_moment_sums_noalloc",
+                "lbm_serve")
 
 #: kernel order of lbm_profile
 PROFILE_STAGES = ("moments", "force", "usolve_sweep", "derivs", "collide")
@@ -51,6 +52,21 @@ class lbm_stats(ctypes.Structure):
                 ("usolve_iters_last", ctypes.c_int), ("usolve_iters_max", ctypes.c_int),
                 ("usolve_resid", ctypes.c_double), ("status", ctypes.c_int),
                 ("usolve_sweeps_total", ctypes.c_int64)]
+
+
+class lbm_request(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int), ("dims", ctypes.c_int64 * 3), ("eos", lbm_eos), ("params", lbm_params),
+                ("steps", ctypes.c_int64), ("arrival_s", ctypes.c_double), ("rho_init", ctypes.c_void_p),
+                ("u_init", ctypes.c_void_p), ("rho_out", ctypes.c_void_p), ("u_out", ctypes.c_void_p)]
+
+
+class lbm_request_result(ctypes.Structure):
+    _fields_ = [("admit_s", ctypes.c_double), ("finish_s", ctypes.c_double), ("status", ctypes.c_int),
+                ("steps_done", ctypes.c_int64), ("footprint", ctypes.c_size_t)]
+
+
+class lbm_serve_config(ctypes.Structure):
+    _fields_ = [("memory_budget", ctypes.c_size_t), ("max_active", ctypes.c_int), ("chunk_steps", ctypes.c_int)]
 
 
 class LbmError(RuntimeError):
@@ -221,6 +237,37 @@ def lbm_moment_sums_noalloc(lattice, pops, n_sites, sums, stream=None):
                                                 ctypes.c_void_p(addr(sums)),
                                                 ctypes.c_void_p(int(stream) if stream else 0))
     _check(rc, "lbm_moment_sums_noalloc")
+
+
+def lbm_serve(requests, memory_budget=0, max_active=16, chunk_steps=50):
+    """Run request dicts to completion (continuous batching); returns lbm_request_result[n].
+
+    Each dict has lattice, dims, eos (lbm_eos), params (lbm_params), steps, arrival_s,
+    rho_init (C-contiguous float64 host array) and optionally u_init, rho_out, u_out
+    (float64 host arrays the results are written to)."""
+    n = len(requests)
+    reqs = (lbm_request * max(n, 1))()
+    keep = []
+    for k, r in enumerate(requests):
+        q = reqs[k]
+        q.lattice = int(r["lattice"])
+        q.dims = _dims(r["dims"])
+        q.eos = r["eos"]
+        q.params = r["params"]
+        q.steps = int(r["steps"])
+        q.arrival_s = float(r["arrival_s"])
+        for name in ("rho_init", "u_init", "rho_out", "u_out"):
+            a = r.get(name)
+            if a is not None:
+                ptr, on = _ptr(a, None, name)
+                if on:
+                    raise TypeError("%s must be a host array" % name)
+                keep.append(a)
+                setattr(q, name, ptr)
+    out = (lbm_request_result * max(n, 1))()
+    cfg = lbm_serve_config(int(memory_budget), int(max_active), int(chunk_steps))
+    _check(load_library().lbm_serve(reqs, n, ctypes.byref(cfg), out), "lbm_serve")
+    return list(out)[:n]
 
 
 def lbm_profile(sim, reps=10):

@@ -188,6 +188,10 @@ class Request:
     steps: int
 
 
+#: T/Tc windows of the serving requests: inside the paper's constraints and linearly stable
+SERVING_TR = {D2Q21: (0.99, 0.995), D3Q59: (0.998, 0.999)}
+
+
 def serving_requests(n=256, seed=1, rate=1.0):
     """The mixed request stream of the serving workload (inter-arrival Exp(1/rate))."""
     rng = np.random.default_rng(seed)
@@ -201,7 +205,7 @@ def serving_requests(n=256, seed=1, rate=1.0):
         else:
             side = int(rng.choice(np.arange(32, 129, 16)))
         frac = rng.uniform(0.15, 0.35)
-        lo, hi = (0.95, 0.995) if lat == D2Q21 else (0.985, 0.995)
+        lo, hi = SERVING_TR[lat]
         Tr = rng.uniform(lo, hi)
         steps = int(rng.integers(500, 5001))
         out.append(Request(k, t, lat, side, frac * side, Tr, steps))
@@ -276,3 +280,15 @@ def make_case(name, dims=None, Tr=None, gamma=0.0):
         rho = spinodal(dims, seed=0)
         return Case(name, D3Q59, dims, Tr, kap, prm, rho, gamma=gamma)
     raise KeyError(name)
+
+
+def serving_case(req: Request):
+    """The droplet of one serving request: its lattice and side, radius, T/Tc; tanh width 4
+    (2 below side 64), kappa matched to that width."""
+    d = 2 if req.lattice == D2Q21 else 3
+    dims = (req.side,) * d
+    prm = vdw_lattice_params(req.Tr, req.lattice)
+    width = 4.0 if req.side >= 64 else 2.0
+    kap = kappa_for_width(prm, width)
+    rho = droplet(dims, req.radius, prm.rho_g, prm.rho_l, W=width)
+    return Case("request%d" % req.rid, req.lattice, dims, req.Tr, kap, prm, rho)
