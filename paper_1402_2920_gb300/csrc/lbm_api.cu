@@ -156,6 +156,7 @@ void fill_phys(Phys<T>& q, const DevSim& dv, const lbm_eos& e)
     for (int k = 0; k < 8; ++k) {
         q.w0[k] = T(dv.w0[k]);
         q.off[k] = T(dv.off[k]);
+        q.isc[k] = dv.w0[k] > 0.0 ? T(1.0 / dv.w0[k]) : T(0);
     }
     q.k1 = T(-0.25 * (g + 1.0) * (g + 1.0) / (g - 1.0));
     q.k2 = T((1.0 / 6.0) * (g * g + 4.0 * g + 1.0) / (g - 1.0));
@@ -882,7 +883,7 @@ int lbm_save(lbm_sim* s, const char* path)
     if (zbytes) LBM_CK(cudaMemcpy(buf.data() + pbytes, s->dev.pop0[s->cur], zbytes, cudaMemcpyDeviceToHost));
     LBM_CK(cudaMemcpy(buf.data() + pbytes + zbytes, s->dev.jt_warm, jbytes, cudaMemcpyDeviceToHost));
     CkptHeader h{};
-    std::memcpy(h.magic, "LBM2PH01", 8);
+    std::memcpy(h.magic, "LBM2PH02", 8);
     h.lattice = s->lattice;
     h.storage = s->prm.storage;
     h.usize = int32_t(s->kt.usize);
@@ -909,7 +910,7 @@ int lbm_load(lbm_sim* s, const char* path)
     CkptHeader h{};
     UsolveState u0{};
     bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::fread(&u0, sizeof(u0), 1, fp) == 1;
-    ok = ok && std::memcmp(h.magic, "LBM2PH01", 8) == 0 && h.lattice == s->lattice && h.storage == s->prm.storage &&
+    ok = ok && std::memcmp(h.magic, "LBM2PH02", 8) == 0 && h.lattice == s->lattice && h.storage == s->prm.storage &&
          h.usize == int32_t(s->kt.usize) && h.Q == s->Q && h.dims[0] == s->dims[0] && h.dims[1] == s->dims[1] &&
          h.dims[2] == s->dims[2];
     const size_t N = size_t(s->dev.N);

@@ -54,6 +54,7 @@ struct Phys {
     T rho1, rho3, cs2_1, A, pi_D, A_pi_D, AD_pi, ph0;  // psi-sine: pi/D, A pi/D, A D/pi, phase at rho0
     T cs2_lo, cs2_hi;                     // positive-weight window
     T w0[8], off[8];                      // w_k(c_s^2(rho0)) and w_k rho0 per shell
+    T isc[8];                             // 1 / w_k(c_s^2(rho0)): scale of the half storage
     T k1, k2, k3;                         // prefactors of Sigma (two) and Xi' (Sec. VIII, S11)
     T cf_int, cf_jt, cf_h2, cf_h3, cj;    // (1+g)/(2 cs0), (g-1)/cs0, 1/(2 cs0^2), 1/(6 cs0^3), (1-g) cs0
 };

@@ -62,7 +62,7 @@ struct Codec;
 template <>
 struct Codec<ST_F32> {
     using type = float;
-    static constexpr bool DEV = false, SPLIT0 = true, EXACT = true;
+    static constexpr bool DEV = false, SPLIT0 = true, EXACT = true, SCALED = false;
     template <typename T>
     __device__ static T raw(const type* p, long long k) { return T(p[k]); }
     template <typename T>
@@ -73,7 +73,7 @@ struct Codec<ST_F32> {
 template <>
 struct Codec<ST_F32_DEV> {
     using type = float;
-    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true;
+    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true, SCALED = false;
     template <typename T>
     __device__ static T raw(const type* p, long long k) { return T(p[k]); }
     template <typename T>
@@ -84,7 +84,9 @@ struct Codec<ST_F32_DEV> {
 template <>
 struct Codec<ST_F16_DEV> {
     using type = __half;
-    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true;
+    // SCALED: the half holds (n_i - w_i rho0) / w_i(rho0), which keeps the small deviations of
+    // the outer shells (weights down to ~1e-5) out of the subnormal range of half
+    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true, SCALED = true;
     template <typename T>
     __device__ static T raw(const type* p, long long k) { return T(__half2float(p[k])); }
     template <typename T>
@@ -95,7 +97,7 @@ struct Codec<ST_F16_DEV> {
 template <>
 struct Codec<ST_BF16_DEV> {
     using type = __nv_bfloat16;
-    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true;
+    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true, SCALED = false;
     template <typename T>
     __device__ static T raw(const type* p, long long k) { return T(__bfloat162float(p[k])); }
     template <typename T>
@@ -106,7 +108,7 @@ struct Codec<ST_BF16_DEV> {
 template <>
 struct Codec<ST_F64> {
     using type = double;
-    static constexpr bool DEV = false, SPLIT0 = false, EXACT = false;
+    static constexpr bool DEV = false, SPLIT0 = false, EXACT = false, SCALED = false;
     template <typename T>
     __device__ static T raw(const type* p, long long k) { return T(p[k]); }
     template <typename T>
@@ -295,7 +297,7 @@ __device__ __forceinline__ T* mp(void* v) { return static_cast<T*>(v); }
 // Stored value of population i at site s of buffer b: n_i, or n_i - w_i(rho0) rho0.
 // The 16-bit storages keep the rest population (i = 0) in FP32 so that the mass
 // remainder below survives storage.
-template <int S, typename T>
+template <int LAT, int S, typename T>
 __device__ __forceinline__ T pop_raw(const DevSim& p, int b, int i, long long s)
 {
     using C = Codec<S>;
@@ -303,11 +305,14 @@ __device__ __forceinline__ T pop_raw(const DevSim& p, int b, int i, long long s)
         const float2 r = cp<float2>(p.pop0[b])[s];
         return T(r.x) + T(r.y);
     }
-    return C::template raw<T>(cp<typename C::type>(p.pop[b]), (long long)i * p.N + s);
+    const auto* base = cp<typename C::type>(p.pop[b]);
+    // scaled storage: the value is half * w_i(rho0), one float product (the same everywhere)
+    if (C::SCALED) return T(__fmul_rn(C::template raw<float>(base, (long long)i * p.N + s), p.pf.w0[Lat<LAT>::shell(i)]));
+    return C::template raw<T>(base, (long long)i * p.N + s);
 }
 
 // Store v (in the storage's convention) and return the value actually stored.
-template <int S, typename T>
+template <int LAT, int S, typename T>
 __device__ __forceinline__ T pop_put(const DevSim& p, int b, int i, long long s, T v)
 {
     using C = Codec<S>;
@@ -317,7 +322,14 @@ __device__ __forceinline__ T pop_put(const DevSim& p, int b, int i, long long s,
         mp<float2>(p.pop0[b])[s] = make_float2(hi, lo);
         return T(hi) + T(lo);
     }
-    C::template put<T>(mp<typename C::type>(p.pop[b]), (long long)i * p.N + s, v);
+    auto* base = mp<typename C::type>(p.pop[b]);
+    if (C::SCALED) {
+        const int k = Lat<LAT>::shell(i);
+        const float x = __fmul_rn(float(v), p.pf.isc[k]);
+        C::template put<float>(base, (long long)i * p.N + s, x);
+        return T(__fmul_rn(C::template rounded<float>(x), p.pf.w0[k]));
+    }
+    C::template put<T>(base, (long long)i * p.N + s, v);
     return C::template rounded<T>(v);
 }
 
@@ -371,7 +383,7 @@ __global__ void __launch_bounds__(256, 3) k_moments(DevSim p, int src, int pair)
     // all loads first, so that a warp keeps the whole column of Q planes in flight
     T v[L::Q];
 #pragma unroll
-    for (int i = C::EXACT ? 1 : 0; i < L::Q; ++i) v[i] = pop_raw<S, T>(p, src, i, s);
+    for (int i = C::EXACT ? 1 : 0; i < L::Q; ++i) v[i] = pop_raw<LAT, S, T>(p, src, i, s);
 #pragma unroll
     for (int i = C::EXACT ? 1 : 0; i < L::Q; ++i) {
         if (C::EXACT) acc2(hi, lo, float(v[i]));
@@ -693,13 +705,13 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
         const T O = omg * wr * ics2 * uc + w0k * (lin + q.cf_h3 * h3);
         T np = E + O, nm = E - O;
         if (READ) {
-            np += g * pop_raw<S, T>(p, src, i, s);
-            nm += g * pop_raw<S, T>(p, src, i + 1, s);
+            np += g * pop_raw<LAT, S, T>(p, src, i, s);
+            nm += g * pop_raw<LAT, S, T>(p, src, i + 1, s);
         }
         const long long dp = ox[sidx(cx)] + oy[sidx(cy)] + oz[sidx(cz)];
         const long long dm = ox[sidx(-cx)] + oy[sidx(-cy)] + oz[sidx(-cz)];
-        const T sp = pop_put<S, T>(p, src ^ 1, i, dp, np);
-        const T sm = pop_put<S, T>(p, src ^ 1, i + 1, dm, nm);
+        const T sp = pop_put<LAT, S, T>(p, src ^ 1, i, dp, np);
+        const T sm = pop_put<LAT, S, T>(p, src ^ 1, i + 1, dm, nm);
         if (C::EXACT) {
             acc2(sh, sl, float(sp));
             acc2(sh, sl, float(sm));
@@ -723,7 +735,7 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
         two_sum(rh, rl, h2, l2);
         mp<float2>(p.pop0[src ^ 1])[s] = make_float2(h2, l2);
     } else {
-        pop_put<S, T>(p, src ^ 1, 0, s, (C::DEV ? drs : rs) - stored_sum);
+        pop_put<LAT, S, T>(p, src ^ 1, 0, s, (C::DEV ? drs : rs) - stored_sum);
     }
 }
 
@@ -1469,11 +1481,11 @@ __global__ void k_init_eq(DevSim p, const double* rho_in, const double* u_in, in
         const T dev = w * rs * X + w * drs +
                       phys<T>(p).rho0 * dcs2 *
                           (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) + T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
-        stored_sum += double(pop_put<S, T>(p, dst, i, s, C::DEV ? dev : w * rs * (T(1) + X)));
+        stored_sum += double(pop_put<LAT, S, T>(p, dst, i, s, C::DEV ? dev : w * rs * (T(1) + X)));
     }
     // the rest population closes the sum to rho (as the collision does)
     const double rest = (C::DEV ? rho_in[s] - p.rho0 : rho_in[s]) - stored_sum;
-    pop_put<S, double>(p, dst, 0, s, rest);
+    pop_put<LAT, S, double>(p, dst, 0, s, rest);
 }
 
 template <int LAT, typename T, typename U>
@@ -1499,7 +1511,7 @@ __global__ void k_pops_out(DevSim p, int src, double* out)
     if (s >= p.N) return;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
-        out[(long long)i * p.N + s] = pop_raw<S, double>(p, src, i, s) + (C::DEV ? p.off[L::shell(i)] : 0.0);
+        out[(long long)i * p.N + s] = pop_raw<LAT, S, double>(p, src, i, s) + (C::DEV ? p.off[L::shell(i)] : 0.0);
 }
 
 template <int LAT, int S>
@@ -1511,7 +1523,7 @@ __global__ void k_pops_in(DevSim p, const double* in, int dst)
     if (s >= p.N) return;
 #pragma unroll
     for (int i = 0; i < L::Q; ++i)
-        pop_put<S, double>(p, dst, i, s, in[(long long)i * p.N + s] - (C::DEV ? p.off[L::shell(i)] : 0.0));
+        pop_put<LAT, S, double>(p, dst, i, s, in[(long long)i * p.N + s] - (C::DEV ? p.off[L::shell(i)] : 0.0));
 }
 
 // FP64 sums of rho and sum_i n_i c_i: fixed grid, fixed tree, so the result is
@@ -1529,7 +1541,7 @@ __global__ void k_red_partial(DevSim p, int src, double* part)
     for (long long s = blockIdx.x * (long long)RED_BLOCK + threadIdx.x; s < p.N; s += (long long)RED_GRID * RED_BLOCK) {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-            const double v = pop_raw<S, double>(p, src, i, s) + (C::DEV ? p.off[L::shell(i)] : 0.0);
+            const double v = pop_raw<LAT, S, double>(p, src, i, s) + (C::DEV ? p.off[L::shell(i)] : 0.0);
             acc[0] += v;
             acc[1] += L::cx(i) * v;
             acc[2] += L::cy(i) * v;
