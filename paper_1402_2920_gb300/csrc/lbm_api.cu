@@ -8,6 +8,7 @@
 // convergence on the device and sets the loop condition, so a step never
 // returns to the host.
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -584,6 +585,13 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
     s->red_out = s->red_part + kRedGrid * 4;
     dv.red = s->red_part;
     if (rc) { lbm_destroy(s); return rc; }
+    {  // vector (16-byte) copies of the tiled kernels need 16-byte aligned field arrays
+        auto a16 = [](const void* q) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) & 15u) == 0; };
+        bool ok = a16(dv.rho) && a16(dv.j0p) && a16(dv.f) && a16(dv.aux) && a16(dv.jt_warm);
+        for (int pr = 0; pr < 2; ++pr)
+            for (int b = 0; b < 2; ++b) ok = ok && a16(dv.uit[pr][b]);
+        dv.aligned16 = ok ? 1 : 0;
+    }
     // well-defined contents before the first lbm_init
     for (int b = 0; b < 2; ++b) {
         if (cudaMemsetAsync(dv.pop[b], 0, size_t(s->Q) * N * SS, s->stream) != cudaSuccess ||

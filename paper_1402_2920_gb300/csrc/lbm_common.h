@@ -79,6 +79,7 @@ struct DevSim {
     UsolveState* us;      // [2]: pair 0 and pair 1
     unsigned* range;      // [2][2][kRangeSlots]: float bits of min and max density per pair
     int* status;          // error bits
+    int aligned16;        // 1: every field array starts on a 16-byte boundary (vector copies allowed)
     double* red;          // reduction scratch
     // physics
     double gamma, kappa, rho0, cs0;  // cs0 = c_s^2(rho0)

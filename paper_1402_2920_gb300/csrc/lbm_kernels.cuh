@@ -799,7 +799,8 @@ template <int B>
 __device__ __forceinline__ void cp_async(void* sdst, const void* gsrc)
 {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(sdst));
-    if (B == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
+    if (B == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc) : "memory");
+    else if (B == 8) asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
     else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
@@ -899,22 +900,39 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2
     bool bad = false;
     // in-plane offsets of the thread's halo points, wrapped once (true modulo: the halo of a
     // small lattice may exceed it)
-    constexpr int MU = (UP + NT - 1) / NT;
-    int hoff[MU];
+    // The halo box starts at x0 - 4, a multiple of 4.  When nx is a multiple of the group G, every
+    // group of G consecutive box columns is G consecutive, aligned sites of the lattice (the
+    // periodic wrap moves whole groups), and goes in one 16-byte copy per field; otherwise the
+    // box goes element by element.
+    constexpr int G = 16 / (sizeof(U) > sizeof(T) ? sizeof(U) : sizeof(T));
+    constexpr int NG = UP / G, MG = (NG + NT - 1) / NT;
+    static_assert(UX % G == 0, "box rows hold whole groups");
+    const bool vec = p.aligned16 && p.nx % G == 0;
+    int goff[MG];  // in-plane lattice offset of the thread's groups
 #pragma unroll
-    for (int m = 0; m < MU; ++m) {
-        const int k = tid + m * NT;
-        hoff[m] = k < UP ? wrapm(x0 - 4 + k % UX, p.nx) + p.nx * wrapm(y0 - 4 + k / UX, p.ny) : 0;
+    for (int m = 0; m < MG; ++m) {
+        const int t = tid + m * NT, gx = t % (UX / G) * G, gy = t / (UX / G);
+        goff[m] = t < NG ? wrapm(x0 - 4 + gx, p.nx) + p.nx * wrapm(y0 - 4 + gy, p.ny) : 0;
     }
     auto fetch = [&](int zl) {
         const long long base = D == 3 ? (long long)wrapc(zl, p.nz) * NP : 0;
         U* du = su + slot(zl) * D * UP;
         T* dr = sr + slot(zl) * UP;
+        if (vec) {
 #pragma unroll
-        for (int m = 0; m < MU; ++m) {
-            const int k = tid + m * NT;
-            if (k < UP) {
-                const long long g = base + hoff[m];
+            for (int m = 0; m < MG; ++m) {
+                const int t = tid + m * NT;
+                if (t < NG) {
+                    const int k = t * G;  // box index of the group's first column
+                    const long long g = base + goff[m];
+#pragma unroll
+                    for (int a = 0; a < D; ++a) cp_async<G * sizeof(U)>(du + a * UP + k, uold + a * p.N + g);
+                    cp_async<G * sizeof(T)>(dr + k, drho + g);
+                }
+            }
+        } else {
+            for (int k = tid; k < UP; k += NT) {
+                const long long g = base + wrapm(x0 - 4 + k % UX, p.nx) + (long long)p.nx * wrapm(y0 - 4 + k / UX, p.ny);
 #pragma unroll
                 for (int a = 0; a < D; ++a) cp_async<sizeof(U)>(du + a * UP + k, uold + a * p.N + g);
                 cp_async<sizeof(T)>(dr + k, drho + g);
