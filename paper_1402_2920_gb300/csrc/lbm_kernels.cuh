@@ -1138,20 +1138,28 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_force(DevSim p, 
     const int gx = x0 + ix, gy = y0 + iy;
     const bool own = gx < p.nx && gy < p.ny;
     const long long own_xy = (long long)gy * p.nx + gx;
-    constexpr int MR = (RP + NT - 1) / NT;
-    int hoff[MR];  // wrapped in-plane offsets of the halo points
+    // pairs of box columns in one copy when nx is even (see the collision kernel's ring)
+    constexpr int G = 2, NG = RP / G, MG = (NG + NT - 1) / NT;
+    const bool vec = p.aligned16 && p.nx % G == 0;
+    int goff[MG];
 #pragma unroll
-    for (int m = 0; m < MR; ++m) {
-        const int k = tid + m * NT;
-        hoff[m] = k < RP ? wrapm(x0 - 2 + k % RX, p.nx) + p.nx * wrapm(y0 - 2 + k / RX, p.ny) : 0;
+    for (int m = 0; m < MG; ++m) {
+        const int t = tid + m * NT, gx = t % (RX / G) * G, gy = t / (RX / G);
+        goff[m] = t < NG ? wrapm(x0 - 2 + gx, p.nx) + p.nx * wrapm(y0 - 2 + gy, p.ny) : 0;
     }
     auto fetch = [&](int zl) {
         const long long base = D == 3 ? (long long)wrapc(zl, p.nz) * NP : 0;
         T* dst = sr + FP::slot(zl) * RP;
+        if (vec) {
 #pragma unroll
-        for (int m = 0; m < MR; ++m) {
-            const int k = tid + m * NT;
-            if (k < RP) cp_async<sizeof(T)>(dst + k, drho + base + hoff[m]);
+            for (int m = 0; m < MG; ++m) {
+                const int t = tid + m * NT;
+                if (t < NG) cp_async<G * sizeof(T)>(dst + t * G, drho + base + goff[m]);
+            }
+        } else {
+            for (int k = tid; k < RP; k += NT)
+                cp_async<sizeof(T)>(dst + k, drho + base + wrapm(x0 - 2 + k % RX, p.nx) +
+                                                 (long long)p.nx * wrapm(y0 - 2 + k / RX, p.ny));
         }
     };
     // own-site inputs (j0, warm-start j~), fetched one plane ahead
@@ -1365,22 +1373,34 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
     U* jw = mp<U>(p.jt_warm);
     T k1, k2, k3;
     collision_consts<LAT, T>(p, k1, k2, k3);
-    constexpr int MR = (RX * RY + TL::THREADS - 1) / TL::THREADS;
-    int hoff[MR];  // wrapped in-plane offsets of the halo points
+    // The halo box starts at x0 - 2, an even column: with nx even, each pair of box columns is
+    // two aligned lattice sites (the periodic wrap moves whole pairs) and goes in one copy.
+    constexpr int G = 2, NG = RX * RY / G, MG = (NG + TL::THREADS - 1) / TL::THREADS;
+    const bool vec = p.aligned16 && p.nx % G == 0;
+    int goff[MG];  // in-plane lattice offset of the thread's pairs
 #pragma unroll
-    for (int m = 0; m < MR; ++m) {
-        const int k = tid + m * nth;
-        hoff[m] = k < RX * RY ? wrapm(x0 - 2 + k % RX, p.nx) + p.nx * wrapm(y0 - 2 + k / RX, p.ny) : 0;
+    for (int m = 0; m < MG; ++m) {
+        const int t = tid + m * nth, gx = t % (RX / G) * G, gy = t / (RX / G);
+        goff[m] = t < NG ? wrapm(x0 - 2 + gx, p.nx) + p.nx * wrapm(y0 - 2 + gy, p.ny) : 0;
     }
     // A, B, C of plane zl into its ring slot, asynchronously
     auto fetch = [&](int zl) {
         const long long base = D == 3 ? (long long)wrapc(zl, p.nz) * p.nx * p.ny : 0;
         T* dst = sr + CollidePlan<D>::slot(zl) * NP * RY * RX;
+        if (vec) {
 #pragma unroll
-        for (int m = 0; m < MR; ++m) {
-            const int k = tid + m * nth;
-            if (k < RX * RY) {
-                const long long g = base + hoff[m];
+            for (int m = 0; m < MG; ++m) {
+                const int t = tid + m * nth;
+                if (t < NG) {
+                    const long long g = base + goff[m];
+#pragma unroll
+                    for (int c = 0; c < NP; ++c)
+                        cp_async<G * sizeof(T)>(dst + c * RY * RX + t * G, aux + (AL::A + c) * p.N + g);
+                }
+            }
+        } else {
+            for (int k = tid; k < RX * RY; k += nth) {
+                const long long g = base + wrapm(x0 - 2 + k % RX, p.nx) + (long long)p.nx * wrapm(y0 - 2 + k / RX, p.ny);
 #pragma unroll
                 for (int c = 0; c < NP; ++c) cp_async<sizeof(T)>(dst + c * RY * RX + k, aux + (AL::A + c) * p.N + g);
             }
