@@ -804,6 +804,8 @@ __device__ __forceinline__ void cp_async(void* sdst, const void* gsrc)
     else asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Ask L2 to fetch the line holding p (no register, no completion to wait for).
+__device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p)); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
@@ -1420,6 +1422,21 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
         cp_async_wait<PF>();
         __syncthreads();
         const int zc = zl - HZ;
+        if (zc + 1 >= z0 && zc + 1 < z1 && tid < TX * TY) {
+            // the per-site inputs of the next plane, into L2 while this plane computes
+            const int gx = min(x0 + tid % TX, p.nx - 1), gy = min(y0 + tid / TX, p.ny - 1);
+            const long long sn = at(p, gx, gy, D == 3 ? zc + 1 : 0);
+#pragma unroll
+            for (int c = AL::SIGL; c < AL::XI + AL::NX; ++c) prefetch_l2(aux + c * p.N + sn);
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                prefetch_l2(uu + a * p.N + sn);
+                prefetch_l2(j0p + a * p.N + sn);
+                prefetch_l2(fp + a * p.N + sn);
+            }
+            prefetch_l2(drho + sn);
+            if (Codec<S>::EXACT) prefetch_l2(cp<float>(p.rho_lo) + sn);
+        }
         if (zc >= z0 && zc < z1) {
             const int gz = D == 3 ? zc : 0;
             const T* pl[5];
