@@ -35,6 +35,11 @@ struct UsolveState {
     int pad[2];
 };
 
+// planes ahead of the one in work whose per-site inputs the collision and derivative
+// kernels prefetch into L2 (measured at 256^3)
+constexpr int kCollideLead = 1;
+constexpr int kDerivsLead = 1;
+
 // slots of the density-range reduction (spread so that block atomics do not contend)
 constexpr int kRangeSlots = 64;
 

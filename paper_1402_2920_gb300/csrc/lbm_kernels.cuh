@@ -1293,6 +1293,13 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
         }
         __syncthreads();
         const int zc = zl - HZ;
+        if (zc + kDerivsLead >= z0 && zc + kDerivsLead < z1 && tid < TX * TY) {
+            // j0' of a plane ahead, into L2 while this plane computes
+            const int gx = min(x0 + tid % TX, p.nx - 1), gy = min(y0 + tid / TX, p.ny - 1);
+            const long long sn = at(p, gx, gy, D == 3 ? zc + kDerivsLead : 0);
+#pragma unroll
+            for (int a = 0; a < D; ++a) prefetch_l2(j0p + a * p.N + sn);
+        }
         if (zc >= z0 && zc < z1) {
             const int gz = D == 3 ? zc : 0;
             const T* pl[5];
@@ -1422,10 +1429,10 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
         cp_async_wait<PF>();
         __syncthreads();
         const int zc = zl - HZ;
-        if (zc + 1 >= z0 && zc + 1 < z1 && tid < TX * TY) {
-            // the per-site inputs of the next plane, into L2 while this plane computes
+        if (zc + kCollideLead >= z0 && zc + kCollideLead < z1 && tid < TX * TY) {
+            // the per-site inputs of a plane ahead, into L2 while this plane computes
             const int gx = min(x0 + tid % TX, p.nx - 1), gy = min(y0 + tid / TX, p.ny - 1);
-            const long long sn = at(p, gx, gy, D == 3 ? zc + 1 : 0);
+            const long long sn = at(p, gx, gy, D == 3 ? zc + kCollideLead : 0);
 #pragma unroll
             for (int c = AL::SIGL; c < AL::XI + AL::NX; ++c) prefetch_l2(aux + c * p.N + sn);
 #pragma unroll
