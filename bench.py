@@ -135,6 +135,22 @@ def _traffic(kernel, workload):
     return None
 
 
+def max_over_ranks(x, dist=None, device="cuda"):
+    """The largest value of x over the ranks (the slowest replica sets the job's time)."""
+    if dist is None:
+        return float(x)
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(world, sites, steps, seconds):
+    """Site updates of all replicas (each runs the same workload) per second of the slowest, in millions."""
+    return world * sites * steps / seconds / 1e6
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -151,13 +167,27 @@ def run_reference(args):
     from oracle import oracle as O
     from paper_1402_2920_gb300 import workloads as W
 
-    n = args.ref_side
-    case = W.make_case("spinodal3d", dims=(n, n, n))
-    a, b, T = case.eos_abT
     cores = os.cpu_count() or 1
     O.set_num_threads(cores)
-    o = O.Sim(case.lattice, case.dims, O.EOS_VDW, O.eos_params(O.EOS_VDW, a=a, b=b, T=T), case.gamma, case.kappa,
-              case.rho0, tol=1e-14)
+
+    def make(n):
+        case = W.make_case("spinodal3d", dims=(n, n, n))
+        a, b, T = case.eos_abT
+        return case, O.Sim(case.lattice, case.dims, O.EOS_VDW, O.eos_params(O.EOS_VDW, a=a, b=b, T=T), case.gamma,
+                           case.kappa, case.rho0, tol=1e-14)
+
+    n = args.ref_side
+    if n <= 0:
+        # size the per-step sample so that the warm-up and timed steps take about two minutes:
+        # one step of a 32^3 cube gives the oracle's rate on these cores
+        case, o = make(32)
+        o.init(case.rho)
+        t0 = time.perf_counter()
+        o.step(1)
+        rate = 32 ** 3 / max(time.perf_counter() - t0, 1e-6)
+        n = int((120.0 * rate / max(args.steps + args.warmup, 1)) ** (1.0 / 3.0))
+        n = max(16, min(64, n))
+    case, o = make(n)
     o.init(case.rho)
     o.step(args.warmup)
     t0 = time.perf_counter()
@@ -254,10 +284,7 @@ def run_native(args):
         rc = P.lbm_sync(sim.handle)
         if rc != 0:
             raise RuntimeError("device reported: " + P.lbm_error_string(rc))
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist)
         sweeps = s_after.usolve_sweeps_total - s_before.usolve_sweeps_total
         return ms, clocks, sweeps, s_after
 
@@ -265,7 +292,7 @@ def run_native(args):
     N = int(np.prod(case.dims))
     sim = make_sim(storage)
     ms, clocks, sweeps, st = timed(sim, K, Wm)
-    mlups = ws * N * K / (ms / 1e3) / 1e6
+    mlups = whole_job_mlups(ws, N, K, ms / 1e3)
     launches = 5 * K + 2 * sweeps  # moments, force, u-solve start, derivs, collide; sweep + control
 
     # dominant kernel: average launch time from CUDA events on the simulation's stream
@@ -290,7 +317,7 @@ def run_native(args):
         torch.cuda.empty_cache()
         sim16 = make_sim(STORAGES["f16dev"])
         ms16, _, sweeps16, _ = timed(sim16, K, Wm)
-        extra["fp16_dev_storage"] = {"value": ws * N * K / (ms16 / 1e3) / 1e6, "unit": UNIT,
+        extra["fp16_dev_storage"] = {"value": whole_job_mlups(ws, N, K, ms16 / 1e3), "unit": UNIT,
                                      "speedup_vs_f32": ms / ms16, "ms_per_step": ms16 / K}
         del sim16
         torch.cuda.empty_cache()
@@ -309,11 +336,8 @@ def run_native(args):
     P.lbm_fields(sim.handle, out_rho.numpy(), out_u.numpy(), N, 3)
     t1 = time.perf_counter()
     e2e_s = t1 - t0
-    if dist:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * N * K / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": N * 8 / K,
+    e2e_s = max_over_ranks(e2e_s, dist)
+    e2e = {"value": whole_job_mlups(ws, N, K, e2e_s), "unit": UNIT, "h2d_bytes_per_step": N * 8 / K,
            "d2h_bytes_per_step": 4 * N * 8 / K,
            "definition": "lbm_init from pinned host rho, %d steps, lbm_fields (S1-S8) back to pinned host" % K}
 
@@ -363,7 +387,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--storage", choices=sorted(STORAGES), default="f32dev")
-    ap.add_argument("--ref-side", type=int, default=48)
+    # cube side of the oracle's per-step sample (0: sized so the run takes about two minutes)
+    ap.add_argument("--ref-side", type=int, default=0)
     ap.add_argument("--no-extras", action="store_true")
     # the benchmark workload is the 256^3 cube; smaller cubes of the same recipe serve profiling
     ap.add_argument("--side", type=int, default=256)
