@@ -28,8 +28,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS and % of HBM roofline (FP32 vs FP16-storage); p50/p99 request latency"
 UNIT = "MLUPS"
-STORAGES = {"f32": 0, "f32dev": 1, "f16dev": 2, "bf16dev": 3}
-STORAGE_BYTES = {"f32": 4, "f32dev": 4, "f16dev": 2, "bf16dev": 2}
+STORAGES = {"f32": 0, "f32dev": 1, "f16dev": 2, "bf16dev": 3, "f32loc": 5, "f16loc": 6, "bf16loc": 7}
+STORAGE_BYTES = {"f32": 4, "f32dev": 4, "f16dev": 2, "bf16dev": 2, "f32loc": 4, "f16loc": 2, "bf16loc": 2}
 
 
 def _peaks():
@@ -361,11 +361,14 @@ def run_native(args):
     if rank == 0:
         line = {"metric": METRIC, "value": mlups, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": Wm,
                 "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32" if args.storage in ("f32", "f32dev") else args.storage, "data": "synthetic",
+                "dtype": "f32" if args.storage in ("f32", "f32dev", "f32loc") else args.storage, "data": "synthetic",
                 "config": {"workload": "D3Q59 %d^3 periodic spinodal (rho = 1 +- 1%% of noise, seed 0), vdW T/Tc=%g, "
                                        "kappa=%.5f, gamma=0" % (n, case.Tr, case.kappa),
                            "storage": {"f32": "FP32 populations", "f32dev": "FP32 deviations n_i - w_i(rho0) rho0",
-                                       "f16dev": "FP16 deviations", "bf16dev": "BF16 deviations"}[args.storage],
+                                       "f16dev": "FP16 deviations", "bf16dev": "BF16 deviations",
+                                       "f32loc": "FP32 deviations from the sender's w_i(rho) rho",
+                                       "f16loc": "FP16 deviations from the sender's w_i(rho) rho",
+                                       "bf16loc": "BF16 deviations from the sender's w_i(rho) rho"}[args.storage],
                            "usolve": "FP32 sweeps, Chebyshev-accelerated for the spectrum [0, g], |dj~| <= 5e-9",
                            "parallelism": "replicas x%d" % ws, "l2": "inputs (populations %.1f GB) larger than L2" % (2 * 59 * STORAGE_BYTES[args.storage] * N / 2 / 1e9),
                            "sites": N},

@@ -43,9 +43,14 @@ enum { LBM_EOS_VDW = 0, LBM_EOS_PSI_SINE = 1 };
 
 /* Population storage.  F32: n_i as float.  F32_DEV / F16_DEV / BF16_DEV: the
  * deviation n_i - w_i(rho0) rho0 as float / half / bfloat16, with FP32
- * arithmetic.  F64: n_i as double with FP64 arithmetic throughout. */
+ * arithmetic.  F64: n_i as double with FP64 arithmetic throughout.
+ * F32_LOC / F16_LOC / BF16_LOC: the deviation n_i - w_i(c_s^2(rho_r)) rho_r from the
+ * local equilibrium weight of the site r that sent the population (its last
+ * collision), which keeps only the velocity and non-equilibrium parts of n_i for
+ * rounding; the library keeps each site's w_k rho per shell (8 floats per site and
+ * buffer in 3D, 6 in 2D).  These run the u-solve in FP32 (LBM_USOLVE_F64 is refused). */
 enum { LBM_STORE_F32 = 0, LBM_STORE_F32_DEV = 1, LBM_STORE_F16_DEV = 2, LBM_STORE_BF16_DEV = 3,
-       LBM_STORE_F64 = 4 };
+       LBM_STORE_F64 = 4, LBM_STORE_F32_LOC = 5, LBM_STORE_F16_LOC = 6, LBM_STORE_BF16_LOC = 7 };
 
 /* Arithmetic of the implicit u-solve (Sec. IX): the storage's arithmetic, or
  * FP64 sweeps also for the reduced-precision storages. */
@@ -179,7 +184,8 @@ int lbm_profile(lbm_sim* sim, int reps, double* ms_out, int n);
 /* Synchronise the stream; returns the first device-recorded error as an LBM_E_* code. */
 int lbm_sync(lbm_sim* sim);
 
-/* Checkpoint: populations in storage format, the warm-start j~, the step counter and
+/* Checkpoint: populations in storage format (with the senders' references of the
+ * local-reference storages), the warm-start j~, the step counter and
  * the parameters.  lbm_load requires a simulation created with the same lattice,
  * dims and storage; a loaded run continues bitwise like an uninterrupted one. */
 int lbm_save(lbm_sim* sim, const char* path);

@@ -3,6 +3,8 @@
 
 namespace lbm {
 
+bool get_kernels_d2q21_loc(int storage, bool usolve_f64, bool read_pops, KernelTable* out);
+
 bool get_kernels_d2q21(int storage, bool usolve_f64, bool read_pops, KernelTable* out)
 {
     constexpr int L = 0;
@@ -26,7 +28,7 @@ bool get_kernels_d2q21(int storage, bool usolve_f64, bool read_pops, KernelTable
         *out = make_table<L, double, ST_F64, double>(read_pops);
         return true;
     }
-    return false;
+    return get_kernels_d2q21_loc(storage, usolve_f64, read_pops, out);
 }
 
 }  // namespace lbm

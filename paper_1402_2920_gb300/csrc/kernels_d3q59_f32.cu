@@ -25,12 +25,14 @@ namespace lbm {
 
 bool get_kernels_d3q59_h16(int storage, bool usolve_f64, bool read_pops, KernelTable* out);
 bool get_kernels_d3q59_f64(int storage, bool usolve_f64, bool read_pops, KernelTable* out);
+bool get_kernels_d3q59_loc(int storage, bool usolve_f64, bool read_pops, KernelTable* out);
 
 bool get_kernels_d3q59(int storage, bool usolve_f64, bool read_pops, KernelTable* out)
 {
     return get_kernels_d3q59_f32(storage, usolve_f64, read_pops, out) ||
            get_kernels_d3q59_h16(storage, usolve_f64, read_pops, out) ||
-           get_kernels_d3q59_f64(storage, usolve_f64, read_pops, out);
+           get_kernels_d3q59_f64(storage, usolve_f64, read_pops, out) ||
+           get_kernels_d3q59_loc(storage, usolve_f64, read_pops, out);
 }
 
 }  // namespace lbm

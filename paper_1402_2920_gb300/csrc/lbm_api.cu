@@ -64,6 +64,9 @@ int nblocks(long long N, int block) { return int((N + block - 1) / block); }
 
 // grid of the tiled kernels: one CTA per TX x TY column tile and z-slab
 dim3 tile_grid(const lbm_sim* s);
+dim3 moments_grid(const lbm_sim* s);
+int moments_block(const lbm_sim* s);
+cudaError_t launch_moments(const lbm_sim* s, DevSim dv, int src, int pair);
 
 void host_eos(const lbm_eos& e, double rho, double out[4])
 {
@@ -157,6 +160,7 @@ void fill_phys(Phys<T>& q, const DevSim& dv, const lbm_eos& e)
     for (int k = 0; k < 8; ++k) {
         q.w0[k] = T(dv.w0[k]);
         q.off[k] = T(dv.off[k]);
+        q.offc[k] = T(dv.off[k] - double(T(dv.off[k])));
         q.isc[k] = dv.w0[k] > 0.0 ? T(1.0 / dv.w0[k]) : T(0);
     }
     q.k1 = T(-0.25 * (g + 1.0) * (g + 1.0) / (g - 1.0));
@@ -169,26 +173,35 @@ void fill_phys(Phys<T>& q, const DevSim& dv, const lbm_eos& e)
     q.cj = T((1.0 - g) * c0);
 }
 
+bool is_local(int storage)
+{
+    return storage == LBM_STORE_F32_LOC || storage == LBM_STORE_F16_LOC || storage == LBM_STORE_BF16_LOC;
+}
+
 size_t bytes_per_site(int lattice, int storage, size_t* ssize_out = nullptr)
 {
     const int Q = lattice == LBM_D3Q59 ? 59 : 21;
     const int naux = lattice == LBM_D3Q59 ? 26 : 13;
     size_t ssize = 4, tsize = 4;
-    if (storage == LBM_STORE_F16_DEV || storage == LBM_STORE_BF16_DEV) ssize = 2;
+    if (storage == LBM_STORE_F16_DEV || storage == LBM_STORE_BF16_DEV || storage == LBM_STORE_F16_LOC ||
+        storage == LBM_STORE_BF16_LOC)
+        ssize = 2;
     if (storage == LBM_STORE_F64) ssize = tsize = 8;
     if (ssize_out) *ssize_out = ssize;
     const size_t usize = 8;  // worst case: FP64 u-solve
     const size_t rest = storage == LBM_STORE_F64 ? 0 : 2 * 8 + 4;  // two float-pair rest planes, rho_lo
+    // the senders' references of the local-reference storages, one set per population buffer
+    const size_t wref = is_local(storage) ? 2 * (lattice == LBM_D3Q59 ? 8 : 6) * 4 : 0;
     // populations (two buffers), rest planes, rho - rho0, j0', f, aux; u iterates (2 x 2),
     // warm-start j~ and the two Chebyshev update vectors
-    return 2 * Q * ssize + rest + tsize * (1 + 3 + 3 + naux) + usize * (4 * 3 + 3 + 2 * 3);
+    return 2 * Q * ssize + rest + wref + tsize * (1 + 3 + 3 + naux) + usize * (4 * 3 + 3 + 2 * 3);
 }
 
 int validate(int lattice, const int64_t dims[3], int storage)
 {
     if (lattice != LBM_D2Q21 && lattice != LBM_D3Q59) return LBM_E_INVALID_ARG;
     if (!dims) return LBM_E_INVALID_ARG;
-    if (storage < LBM_STORE_F32 || storage > LBM_STORE_F64) return LBM_E_INVALID_ARG;
+    if (storage < LBM_STORE_F32 || storage > LBM_STORE_BF16_LOC) return LBM_E_INVALID_ARG;
     if (dims[0] < 4 || dims[1] < 4) return LBM_E_INVALID_ARG;
     if (lattice == LBM_D2Q21 && dims[2] != 1) return LBM_E_INVALID_ARG;
     if (lattice == LBM_D3Q59 && dims[2] < 4) return LBM_E_INVALID_ARG;
@@ -227,7 +240,7 @@ int add_step(lbm_sim* s, cudaGraph_t g, cudaGraphNode_t dep, int src, cudaGraphN
     size_t nd0 = dep ? 1 : 0;
     {
         void* a[] = {&dv, &src, &pair};
-        LBM_CK(add_kernel(g, &n1, s->kt.moments, dim3(G), B, a, d0, nd0));
+        LBM_CK(add_kernel(g, &n1, s->kt.moments, moments_grid(s), moments_block(s), a, d0, nd0));
     }
     const dim3 TG = tile_grid(s);
     const int TB = s->kt.tile_threads;
@@ -354,6 +367,22 @@ int reset_usolve(lbm_sim* s)
     return LBM_OK;
 }
 
+// moments kernel: flat grid, or for the local-reference storages the row grid (x-blocks of
+// kMomentsRowBlock threads, y, z), which gives each thread its coordinates
+constexpr int kMomentsRowBlock = 128;
+dim3 moments_grid(const lbm_sim* s)
+{
+    if (!s->kt.local_ref) return dim3(nblocks(s->dev.N, s->kt.block));
+    return dim3((s->dev.nx + kMomentsRowBlock - 1) / kMomentsRowBlock, s->dev.ny, s->d == 3 ? s->dev.nz : 1);
+}
+int moments_block(const lbm_sim* s) { return s->kt.local_ref ? kMomentsRowBlock : s->kt.block; }
+
+cudaError_t launch_moments(const lbm_sim* s, DevSim dv, int src, int pair)
+{
+    void* a[] = {&dv, &src, &pair};
+    return cudaLaunchKernel(s->kt.moments, moments_grid(s), dim3(moments_block(s)), a, 0, s->stream);
+}
+
 dim3 tile_grid(const lbm_sim* s)
 {
     const int* t = s->kt.tile;
@@ -367,7 +396,7 @@ int run_fields(lbm_sim* s)
     DevSim& dv = s->dev;
     const int B = s->kt.block, G = nblocks(dv.N, B);
     const int pair = 1;
-    LBM_CK(launch(s, s->kt.moments, G, B, dv, s->cur, pair));
+    LBM_CK(launch_moments(s, dv, s->cur, pair));
     LBM_CK(launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair));
     LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
     cudaGraphConditionalHandle h{};
@@ -565,6 +594,14 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
     for (int pr = 0; pr < 2; ++pr)
         for (int b = 0; b < 2; ++b) rc = rc ? rc : dev_alloc(s, &dv.uit[pr][b], 3 * N * U);
     rc = rc ? rc : dev_alloc(s, &dv.jt_warm, 3 * N * U);
+    if (s->kt.local_ref) {
+        const int nshell = lattice == LBM_D3Q59 ? 8 : 6;
+        for (int b = 0; b < 2; ++b) {
+            void* w = nullptr;
+            rc = rc ? rc : dev_alloc(s, &w, size_t(nshell) * N * sizeof(float));
+            dv.wref[b] = static_cast<float*>(w);
+        }
+    }
     if (dv.cheb) {
         rc = rc ? rc : dev_alloc(s, &dv.dvec[0], 3 * N * U);
         rc = rc ? rc : dev_alloc(s, &dv.dvec[1], 3 * N * U);
@@ -594,8 +631,10 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
     }
     // well-defined contents before the first lbm_init
     for (int b = 0; b < 2; ++b) {
+        const size_t wbytes = dv.wref[b] ? size_t(lattice == LBM_D3Q59 ? 8 : 6) * N * sizeof(float) : 0;
         if (cudaMemsetAsync(dv.pop[b], 0, size_t(s->Q) * N * SS, s->stream) != cudaSuccess ||
-            (dv.pop0[b] && cudaMemsetAsync(dv.pop0[b], 0, N * s->kt.rsize, s->stream) != cudaSuccess)) {
+            (dv.pop0[b] && cudaMemsetAsync(dv.pop0[b], 0, N * s->kt.rsize, s->stream) != cudaSuccess) ||
+            (wbytes && cudaMemsetAsync(dv.wref[b], 0, wbytes, s->stream) != cudaSuccess)) {
             lbm_destroy(s);
             return LBM_E_CUDA;
         }
@@ -630,6 +669,7 @@ int lbm_init(lbm_sim* s, const double* rho, const double* u, int on_device)
     s->cur = 0;
     s->steps = 0;
     const int B = s->kt.block, G = nblocks(s->dev.N, B);
+    if (s->kt.init_ref) LBM_CK(launch(s, s->kt.init_ref, G, B, s->dev, drho, 0));
     LBM_CK(launch(s, s->kt.init_eq, G, B, s->dev, drho, du, 0));
     if (tmp) LBM_CK(cudaFreeAsync(tmp, s->stream));
     return LBM_OK;
@@ -653,7 +693,7 @@ int step_direct(lbm_sim* s)
     const int B = s->kt.block, G = nblocks(dv.N, B);
     const int pair = 0, no = 0, src = s->cur;
     cudaGraphConditionalHandle h{};
-    LBM_CK(launch(s, s->kt.moments, G, B, dv, src, pair));
+    LBM_CK(launch_moments(s, dv, src, pair));
     LBM_CK(launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair));
     LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
     for (int it = 0; it < dv.maxit + 1; ++it) {
@@ -781,7 +821,16 @@ int lbm_set_populations(lbm_sim* s, const double* in, int on_device)
     if (rc) return rc;
     s->cur = 0;
     const int B = s->kt.block, G = nblocks(s->dev.N, B);
+    double* rho = nullptr;
+    if (s->kt.init_ref) {
+        // local-reference storages: every site's references from the density of the given
+        // populations, then the populations relative to their senders'
+        LBM_CK(cudaMallocAsync(&rho, size_t(s->dev.N) * sizeof(double), s->stream));
+        LBM_CK(launch(s, s->kt.pops_rho, G, B, s->dev, d, rho));
+        LBM_CK(launch(s, s->kt.init_ref, G, B, s->dev, (const double*)rho, 0));
+    }
     LBM_CK(launch(s, s->kt.pops_in, G, B, s->dev, d, 0));
+    if (rho) LBM_CK(cudaFreeAsync(rho, s->stream));
     if (tmp) LBM_CK(cudaFreeAsync(tmp, s->stream));
     LBM_CK(cudaStreamSynchronize(s->stream));
     return LBM_OK;
@@ -829,7 +878,7 @@ int lbm_profile(lbm_sim* s, int reps, double* ms_out, int n)
     LBM_CK(cudaEventCreate(&e0));
     LBM_CK(cudaEventCreate(&e1));
     // the scratch u-solve pair; the collision writes the spare population buffer
-    LBM_CK(launch(s, s->kt.moments, G, B, dv, src, pair));
+    LBM_CK(launch_moments(s, dv, src, pair));
     LBM_CK(launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair));
     LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
     int rc = LBM_OK;
@@ -838,7 +887,7 @@ int lbm_profile(lbm_sim* s, int reps, double* ms_out, int n)
             if (r == 1 && cudaEventRecord(e0, s->stream) != cudaSuccess) rc = LBM_E_CUDA;
             cudaError_t e = cudaSuccess;
             switch (k) {
-            case 0: e = launch(s, s->kt.moments, G, B, dv, src, pair); break;
+            case 0: e = launch_moments(s, dv, src, pair); break;
             case 1: e = launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair); break;
             case 2: e = launch_tiled(s, s->kt.sweep, s->kt.smem_sweep, dv, pair); break;
             case 3: e = launch_tiled(s, s->kt.derivs, s->kt.smem_derivs, dv); break;
@@ -884,12 +933,15 @@ int lbm_save(lbm_sim* s, const char* path)
     const size_t pbytes = size_t(s->Q) * N * s->kt.ssize;
     const size_t zbytes = N * s->kt.rsize;
     const size_t jbytes = 3 * N * s->kt.usize;
-    std::vector<char> buf(pbytes + zbytes + jbytes);
+    const size_t wbytes = s->dev.wref[0] ? size_t(s->d == 3 ? 8 : 6) * N * sizeof(float) : 0;
+    std::vector<char> buf(pbytes + zbytes + jbytes + wbytes);
     UsolveState us[2];
     LBM_CK(cudaMemcpy(us, s->dev.us, sizeof(us), cudaMemcpyDeviceToHost));
     LBM_CK(cudaMemcpy(buf.data(), s->dev.pop[s->cur], pbytes, cudaMemcpyDeviceToHost));
     if (zbytes) LBM_CK(cudaMemcpy(buf.data() + pbytes, s->dev.pop0[s->cur], zbytes, cudaMemcpyDeviceToHost));
     LBM_CK(cudaMemcpy(buf.data() + pbytes + zbytes, s->dev.jt_warm, jbytes, cudaMemcpyDeviceToHost));
+    if (wbytes)  // the senders' references the stored populations are relative to
+        LBM_CK(cudaMemcpy(buf.data() + pbytes + zbytes + jbytes, s->dev.wref[s->cur], wbytes, cudaMemcpyDeviceToHost));
     CkptHeader h{};
     std::memcpy(h.magic, "LBM2PH02", 8);
     h.lattice = s->lattice;
@@ -925,9 +977,10 @@ int lbm_load(lbm_sim* s, const char* path)
     const size_t pbytes = size_t(s->Q) * N * s->kt.ssize;
     const size_t zbytes = N * s->kt.rsize;
     const size_t jbytes = 3 * N * s->kt.usize;
+    const size_t wbytes = s->dev.wref[0] ? size_t(s->d == 3 ? 8 : 6) * N * sizeof(float) : 0;
     std::vector<char> buf;
     if (ok) {
-        buf.resize(pbytes + zbytes + jbytes);
+        buf.resize(pbytes + zbytes + jbytes + wbytes);
         ok = std::fread(buf.data(), 1, buf.size(), fp) == buf.size();
     }
     std::fclose(fp);
@@ -942,6 +995,7 @@ int lbm_load(lbm_sim* s, const char* path)
     LBM_CK(cudaMemcpy(s->dev.pop[0], buf.data(), pbytes, cudaMemcpyHostToDevice));
     if (zbytes) LBM_CK(cudaMemcpy(s->dev.pop0[0], buf.data() + pbytes, zbytes, cudaMemcpyHostToDevice));
     LBM_CK(cudaMemcpy(s->dev.jt_warm, buf.data() + pbytes + zbytes, jbytes, cudaMemcpyHostToDevice));
+    if (wbytes) LBM_CK(cudaMemcpy(s->dev.wref[0], buf.data() + pbytes + zbytes + jbytes, wbytes, cudaMemcpyHostToDevice));
     LBM_CK(cudaMemcpy(&s->dev.us[0], &u0, sizeof(u0), cudaMemcpyHostToDevice));
     s->steps = h.steps;
     return LBM_OK;

@@ -10,7 +10,8 @@
 
 namespace lbm {
 
-enum Store { ST_F32 = 0, ST_F32_DEV = 1, ST_F16_DEV = 2, ST_BF16_DEV = 3, ST_F64 = 4 };
+enum Store { ST_F32 = 0, ST_F32_DEV = 1, ST_F16_DEV = 2, ST_BF16_DEV = 3, ST_F64 = 4, ST_F32_LOC = 5, ST_F16_LOC = 6,
+             ST_BF16_LOC = 7 };
 
 // Device-resident state of one implicit u-solve (Sec. IX): which of the two
 // j~ buffers is current, the sweep counter and the residual reductions.
@@ -60,6 +61,7 @@ struct Phys {
     T cs2_lo, cs2_hi;                     // positive-weight window
     T w0[8], off[8];                      // w_k(c_s^2(rho0)) and w_k rho0 per shell
     T isc[8];                             // 1 / w_k(c_s^2(rho0)): scale of the half storage
+    T offc[8];                            // w_k rho0 (FP64) minus off[k] in this precision
     T k1, k2, k3;                         // prefactors of Sigma (two) and Xi' (Sec. VIII, S11)
     T cf_int, cf_jt, cf_h2, cf_h3, cj;    // (1+g)/(2 cs0), (g-1)/cs0, 1/(2 cs0^2), 1/(6 cs0^3), (1-g) cs0
 };
@@ -81,6 +83,8 @@ struct DevSim {
                           // and pair 1 (lbm_fields); u = (j0' + j~)/rho (S3)
     void* jt_warm;        // U [3][N]: j~ = rho u - j0' of the last step, the warm start (Sec. IX)
     void* aux;            // T [26][N]: A, B_ab, C_a, the local part of Sigma_ab, Xi'_abc
+    float* wref[2];       // [NSHELL][N] per population buffer (local-reference storages): w_k(c_s^2(rho)) rho
+                          // of every site at the collision that sent the populations in that buffer
     UsolveState* us;      // [2]: pair 0 and pair 1
     unsigned* range;      // [2][2][kRangeSlots]: float bits of min and max density per pair
     int* status;          // error bits
@@ -115,6 +119,8 @@ struct KernelTable {
     const void* derivs;       // (DevSim)
     const void* collide;      // (DevSim, int src)
     const void* init_eq;      // (DevSim, const double* rho, const double* u, int dst)
+    const void* init_ref;     // (DevSim, const double* rho, int dst): local-reference storages only
+    const void* pops_rho;     // (DevSim, const double* pops, double* rho): sum over i of FP64 populations
     const void* fields_out;   // (DevSim, int pair, double* rho, double* u)
     const void* pops_out;     // (DevSim, int src, double* out)
     const void* pops_in;      // (DevSim, const double* in, int dst)
@@ -126,7 +132,8 @@ struct KernelTable {
     size_t smem_force, smem_sweep, smem_derivs, smem_collide;  // dynamic shared memory bytes
     size_t tsize, usize, ssize;  // bytes of T, U and the storage type
     size_t rsize;                // bytes of a rest-plane element (0: no separate plane)
-    bool exact;                  // FP64 density bookkeeping (rho_lo is used)
+    bool exact;                  // float-pair density bookkeeping (rho_lo is used)
+    bool local_ref;              // the storage is relative to the sender's w_k rho (DevSim::wref)
 };
 
 // Exported by the lattice translation units.

@@ -62,7 +62,7 @@ struct Codec;
 template <>
 struct Codec<ST_F32> {
     using type = float;
-    static constexpr bool DEV = false, SPLIT0 = true, EXACT = true, SCALED = false;
+    static constexpr bool DEV = false, SPLIT0 = true, EXACT = true, SCALED = false, LOC = false;
     template <typename T>
     __device__ static T raw(const type* p, long long k) { return T(p[k]); }
     template <typename T>
@@ -73,7 +73,7 @@ struct Codec<ST_F32> {
 template <>
 struct Codec<ST_F32_DEV> {
     using type = float;
-    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true, SCALED = false;
+    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true, SCALED = false, LOC = false;
     template <typename T>
     __device__ static T raw(const type* p, long long k) { return T(p[k]); }
     template <typename T>
@@ -86,7 +86,7 @@ struct Codec<ST_F16_DEV> {
     using type = __half;
     // SCALED: the half holds (n_i - w_i rho0) / w_i(rho0), which keeps the small deviations of
     // the outer shells (weights down to ~1e-5) out of the subnormal range of half
-    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true, SCALED = true;
+    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true, SCALED = true, LOC = false;
     template <typename T>
     __device__ static T raw(const type* p, long long k) { return T(__half2float(p[k])); }
     template <typename T>
@@ -97,7 +97,7 @@ struct Codec<ST_F16_DEV> {
 template <>
 struct Codec<ST_BF16_DEV> {
     using type = __nv_bfloat16;
-    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true, SCALED = false;
+    static constexpr bool DEV = true, SPLIT0 = true, EXACT = true, SCALED = false, LOC = false;
     template <typename T>
     __device__ static T raw(const type* p, long long k) { return T(__bfloat162float(p[k])); }
     template <typename T>
@@ -108,13 +108,31 @@ struct Codec<ST_BF16_DEV> {
 template <>
 struct Codec<ST_F64> {
     using type = double;
-    static constexpr bool DEV = false, SPLIT0 = false, EXACT = false, SCALED = false;
+    static constexpr bool DEV = false, SPLIT0 = false, EXACT = false, SCALED = false, LOC = false;
     template <typename T>
     __device__ static T raw(const type* p, long long k) { return T(p[k]); }
     template <typename T>
     __device__ static void put(type* p, long long k, T v) { p[k] = double(v); }
     template <typename T>
     __device__ static T rounded(T v) { return T(double(v)); }
+};
+
+// Local-reference storages: the stored value is n_i - w_i(c_s^2(rho_r)) rho_r with r the site that
+// sent the population (its last collision), so only the part of n_i that the local equilibrium
+// weight does not carry is rounded: the velocity and non-equilibrium parts, ~1e-3 of n_i,
+// instead of the 10-20 % of n_i by which a two-phase density field departs from w_i(rho0) rho0.
+// The sender's references w_k rho_r per shell live in DevSim::wref.
+template <>
+struct Codec<ST_F32_LOC> : Codec<ST_F32_DEV> {
+    static constexpr bool LOC = true;
+};
+template <>
+struct Codec<ST_F16_LOC> : Codec<ST_F16_DEV> {
+    static constexpr bool LOC = true;  // scaled by 1/w_i(rho0) as well: the values are small
+};
+template <>
+struct Codec<ST_BF16_LOC> : Codec<ST_BF16_DEV> {
+    static constexpr bool LOC = true;
 };
 
 template <typename T>
@@ -225,6 +243,14 @@ __device__ __forceinline__ long long at(const DevSim& p, int x, int y, int z)
 __device__ __forceinline__ long long shifted(const DevSim& p, const Site& r, int dx, int dy, int dz)
 {
     return at(p, wrapc(r.x + dx, p.nx), wrapc(r.y + dy, p.ny), wrapc(r.z + dz, p.nz));
+}
+
+// Site that sent population i to site (x, y, z): (x, y, z) - c_i, periodic (|c| <= 4 <= n).
+template <int LAT>
+__device__ __forceinline__ long long sender(const DevSim& p, int x, int y, int z, int i)
+{
+    using L = Lat<LAT>;
+    return at(p, wrapc(x - L::cx(i), p.nx), wrapc(y - L::cy(i), p.ny), L::D == 3 ? wrapc(z - L::cz(i), p.nz) : 0);
 }
 
 // Site indices of r - 2e_a, r - e_a, r + e_a, r + 2e_a for every axis a.
@@ -370,8 +396,20 @@ __global__ void __launch_bounds__(256, 3) k_moments(DevSim p, int src, int pair)
 {
     using L = Lat<LAT>;
     using C = Codec<S>;
-    const long long s0 = gtid();
-    const long long s = s0 < p.N ? s0 : p.N - 1;  // the tail recomputes the last site (same values)
+    // local-reference storages run on the row grid (x-blocks, y, z), which hands each thread its
+    // coordinates; the others on a flat grid
+    int x = 0, y = 0, z = 0;
+    long long s0;
+    if (C::LOC) {
+        x = int(blockIdx.x * blockDim.x + threadIdx.x);
+        y = int(blockIdx.y);
+        z = int(blockIdx.z);
+        s0 = x < p.nx ? at(p, x, y, z) : p.N;
+        x = min(x, p.nx - 1);
+    } else {
+        s0 = gtid();
+    }
+    const long long s = s0 < p.N ? s0 : (C::LOC ? at(p, x, y, z) : p.N - 1);  // tails recompute a site
     const bool own = s0 < p.N;
     T sum = T(0), j[3] = {T(0), T(0), T(0)};
     float hi = 0.f, lo = 0.f;
@@ -380,23 +418,55 @@ __global__ void __launch_bounds__(256, 3) k_moments(DevSim p, int src, int pair)
         hi = r0.x;
         lo = r0.y;
     }
-    // all loads first, so that a warp keeps the whole column of Q planes in flight
-    T v[L::Q];
+    if (C::LOC) {
+        // n_i = stored_i + the sender's reference w_k rho.  The mass sums the decoded floats
+        // fl(stored + reference), the values the sending collision accounted for; j0 goes over
+        // opposite pairs, where the references enter as differences of neighbouring values.
+        int ox[7], oy[7], oz[7];  // wrapped site offsets for the shifts -4, -2, -1, 0, 1, 2, 4
 #pragma unroll
-    for (int i = C::EXACT ? 1 : 0; i < L::Q; ++i) v[i] = pop_raw<LAT, S, T>(p, src, i, s);
+        for (int k = 0; k < 7; ++k) {
+            const int sh = k == 0 ? -4 : k == 6 ? 4 : k - 3;
+            ox[k] = wrapc(x + sh, p.nx);
+            oy[k] = wrapc(y + sh, p.ny) * p.nx;
+            oz[k] = L::D == 3 ? wrapc(z + sh, p.nz) * p.nx * p.ny : 0;
+        }
+        auto sidx = [](int c) { return c == -4 ? 0 : c == 4 ? 6 : c + 3; };
+        const float* wr = p.wref[src];
+        acc2(hi, lo, wr[s]);  // the rest population's reference: its own site
 #pragma unroll
-    for (int i = C::EXACT ? 1 : 0; i < L::Q; ++i) {
-        if (C::EXACT) acc2(hi, lo, float(v[i]));
-        else sum += v[i];
-        if (L::cx(i)) j[0] += T(L::cx(i)) * v[i];
-        if (L::cy(i)) j[1] += T(L::cy(i)) * v[i];
-        if (L::cz(i)) j[2] += T(L::cz(i)) * v[i];
+        for (int i = 1; i < L::Q; i += 2) {
+            const int k = L::shell(i);
+            const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
+            const float va = float(pop_raw<LAT, S, T>(p, src, i, s)), vb = float(pop_raw<LAT, S, T>(p, src, i + 1, s));
+            // population i came from the site at -c_i, its opposite from +c_i
+            const float ra = wr[k * p.N + ox[sidx(-cx)] + oy[sidx(-cy)] + oz[sidx(-cz)]];
+            const float rb = wr[k * p.N + ox[sidx(cx)] + oy[sidx(cy)] + oz[sidx(cz)]];
+            acc2(hi, lo, __fadd_rn(va, ra));
+            acc2(hi, lo, __fadd_rn(vb, rb));
+            const T d = T(va - vb) + T(ra - rb);
+            if (cx) j[0] += T(cx) * d;
+            if (cy) j[1] += T(cy) * d;
+            if (cz) j[2] += T(cz) * d;
+        }
+    } else {
+        // all loads first, so that a warp keeps the whole column of Q planes in flight
+        T v[L::Q];
+#pragma unroll
+        for (int i = C::EXACT ? 1 : 0; i < L::Q; ++i) v[i] = pop_raw<LAT, S, T>(p, src, i, s);
+#pragma unroll
+        for (int i = C::EXACT ? 1 : 0; i < L::Q; ++i) {
+            if (C::EXACT) acc2(hi, lo, float(v[i]));
+            else sum += v[i];
+            if (L::cx(i)) j[0] += T(L::cx(i)) * v[i];
+            if (L::cy(i)) j[1] += T(L::cy(i)) * v[i];
+            if (L::cz(i)) j[2] += T(L::cz(i)) * v[i];
+        }
     }
     // rho - rho0: the deviation sum itself (sum_i w_i(rho0) rho0 = rho0 and the
     // odd offsets cancel in j0), or sum - rho0
     T drho;
     if (C::EXACT) {
-        if (!C::DEV) {
+        if (!C::DEV || C::LOC) {  // the sum is rho itself
             float e;
             two_sum(hi, -p.pf.rho0, hi, e);
             lo = __fadd_rn(lo, e);
@@ -593,6 +663,27 @@ __device__ __forceinline__ void derivs_tail(const DevSim& p, long long s, const 
             }
 }
 
+// Reference w_k rho of the local-reference storages, as the float nearest to
+// w_k(rho0) rho0 + dw (dw = w_k rho - w_k(rho0) rho0 from the difference formula, accurate to
+// its own size).  corr returns w_k rho - ref: the float rounding of w_k(rho0) rho0 and of the sum,
+// which the stored deviation carries so that deviation + ref is w_k rho to FP32 accuracy of dw.
+__device__ __forceinline__ float local_ref(const Phys<float>& q, int k, float dw, float& corr)
+{
+    float ref, e;
+    two_sum(q.off[k], dw, ref, e);
+    corr = __fadd_rn(q.offc[k], e);
+    return ref;
+}
+
+// velocities in shell k (the rest velocity counts in shell 0)
+template <int LAT>
+__host__ __device__ constexpr int shell_count(int k)
+{
+    int m = 0;
+    for (int i = 0; i < Lat<LAT>::Q; ++i) m += Lat<LAT>::shell(i) == k ? 1 : 0;
+    return m;
+}
+
 // i and i + 1 are opposite velocities for every odd i (the tables' order)
 template <int LAT>
 __host__ __device__ constexpr bool pairs_opposite()
@@ -671,7 +762,15 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
         const T wr = wl * rs;
         const T w0k = q.w0[k];
         T even0;
-        if (C::DEV) {
+        float lref = 0.f, lcorr = 0.f;  // this site's reference for shell k and w rho - reference
+        if (C::LOC) {
+            // n^eq - w rho = w rho X; the stored value is relative to the float reference
+            const T dw0 = wl * drs + q.rho0 * dcs2 *
+                                         (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) +
+                                          T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
+            lref = local_ref(p.pf, k, float(dw0), lcorr);
+            even0 = omg * (wr * B1) + w0k * q.cf_h2 * h2c + T(lcorr);
+        } else if (C::DEV) {
             // n^eq - w(rho0) rho0 = w rho X + w drho + rho0 (w(s) - w(s0)), with
             // w(s) - w(s0) = (s - s0) [c1 + c2 (s + s0) + c3 (s^2 + s s0 + s0^2)]
             const T dw0 = wl * drs + q.rho0 * dcs2 *
@@ -707,12 +806,22 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
         if (READ) {
             np += g * pop_raw<LAT, S, T>(p, src, i, s);
             nm += g * pop_raw<LAT, S, T>(p, src, i + 1, s);
+            if (C::LOC) {  // n - w rho: the stored part, the sender's reference minus this site's
+                const float* wf = p.wref[src];
+                np += g * (T(__fsub_rn(wf[k * p.N + sender<LAT>(p, r.x, r.y, r.z, i)], lref)) - T(lcorr));
+                nm += g * (T(__fsub_rn(wf[k * p.N + sender<LAT>(p, r.x, r.y, r.z, i + 1)], lref)) - T(lcorr));
+            }
         }
         const long long dp = ox[sidx(cx)] + oy[sidx(cy)] + oz[sidx(cz)];
         const long long dm = ox[sidx(-cx)] + oy[sidx(-cy)] + oz[sidx(-cz)];
         const T sp = pop_put<LAT, S, T>(p, src ^ 1, i, dp, np);
         const T sm = pop_put<LAT, S, T>(p, src ^ 1, i + 1, dm, nm);
-        if (C::EXACT) {
+        if (C::LOC) {
+            // the decoded values the next moments kernel will sum: stored part plus this site's
+            // reference, rounded to float the same way there
+            acc2(sh, sl, __fadd_rn(float(sp), lref));
+            acc2(sh, sl, __fadd_rn(float(sm), lref));
+        } else if (C::EXACT) {
             acc2(sh, sl, float(sp));
             acc2(sh, sl, float(sm));
         } else {
@@ -720,10 +829,26 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
             stored_sum += sm;
         }
     }
-    // rest population: the stored convention sums to rho - rho0 (deviations) or rho
+    if (C::LOC) {
+        // this site's references for the populations it sends; the rest population's own
+        // reference joins the float pair (the others are inside the decoded values)
+        float* wf = p.wref[src ^ 1];
+#pragma unroll
+        for (int k = 0; k < L::NSHELL; ++k) {
+            const T wl = weight<LAT, T>(k, cs2);
+            const T dw0 = wl * drs + q.rho0 * dcs2 *
+                                         (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) +
+                                          T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
+            float corr;
+            const float wk = local_ref(p.pf, k, float(dw0), corr);
+            wf[k * p.N + s] = wk;
+            if (k == 0) acc2(sh, sl, wk);
+        }
+    }
+    // rest population: the stored convention sums to rho - rho0 (global deviations) or rho
     if (C::EXACT) {
         float th = float(drs), tl = cp<float>(p.rho_lo)[s];  // the exact pre-collision sum
-        if (!C::DEV) {
+        if (!C::DEV || C::LOC) {
             float e;
             two_sum(th, p.pf.rho0, th, e);
             tl = __fadd_rn(tl, e);
@@ -1513,6 +1638,15 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
 // ---------------------------------------------------------------------------
 // Initial condition, field and population transfer, conservation sums
 // ---------------------------------------------------------------------------
+// w_k(c_s^2(rho)) in FP64 (initialisation only)
+template <int LAT>
+__device__ __forceinline__ double lat_weight_d(int k, const DevSim& p, double rho)
+{
+    double P, DP, PM, RPP;
+    eos_full<double>(p, rho, P, DP, PM, RPP);
+    return weight<LAT, double>(k, P / rho);
+}
+
 template <int LAT, typename T, int S>
 __global__ void k_init_eq(DevSim p, const double* rho_in, const double* u_in, int dst)
 {
@@ -1534,20 +1668,82 @@ __global__ void k_init_eq(DevSim p, const double* rho_in, const double* u_in, in
 #pragma unroll
     for (int a = 0; a < L::D; ++a) uu += u[a] * u[a];
     double stored_sum = 0.0;  // initialisation is not on the hot path: FP64 is fine here
+    const float* wf = C::LOC ? p.wref[dst] : nullptr;
+    const int x = int(s % p.nx), y = int((s / p.nx) % p.ny), z = int(s / ((long long)p.nx * p.ny));
 #pragma unroll
     for (int i = 1; i < L::Q; ++i) {
         const int k = L::shell(i);
         const T uc = T(L::cx(i)) * u[0] + T(L::cy(i)) * u[1] + T(L::cz(i)) * u[2];
         const T X = uc * ics2 + T(0.5) * uc * uc * ics2 * ics2 - T(0.5) * uu * ics2;
         const T w = weight<LAT, T>(k, cs2);
+        if (C::LOC) {
+            // as if sent by the neighbour at -c_i: n^eq here minus that site's reference, in FP64
+            const double ref = double(wf[k * p.N + sender<LAT>(p, x, y, z, i)]);
+            const double wd = lat_weight_d<LAT>(k, p, rho_in[s]) * rho_in[s];
+            const double dev = (wd - ref) + wd * double(X);
+            stored_sum += double(pop_put<LAT, S, double>(p, dst, i, s, dev)) + ref;
+            continue;
+        }
         const T dev = w * rs * X + w * drs +
                       phys<T>(p).rho0 * dcs2 *
                           (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) + T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
         stored_sum += double(pop_put<LAT, S, T>(p, dst, i, s, C::DEV ? dev : w * rs * (T(1) + X)));
     }
     // the rest population closes the sum to rho (as the collision does)
-    const double rest = (C::DEV ? rho_in[s] - p.rho0 : rho_in[s]) - stored_sum;
+    if (C::LOC) stored_sum += double(wf[s]);  // the rest population's own reference
+    const double rest = (C::DEV && !C::LOC ? rho_in[s] - p.rho0 : rho_in[s]) - stored_sum;
     pop_put<LAT, S, double>(p, dst, 0, s, rest);
+}
+
+// The references w_k(c_s^2(rho)) rho of every site for the initial populations (local-reference
+// storages); k_init_eq then stores each population relative to its sender's.
+template <int LAT, typename T>
+__global__ void k_init_ref(DevSim p, const double* rho_in, int dst)
+{
+    using L = Lat<LAT>;
+    const long long s = gtid();
+    if (s >= p.N) return;
+    const T drs = T(rho_in[s] - p.rho0);
+    T cs2, dcs2;
+    cs2_delta<T>(p, drs, cs2, dcs2);
+    const T cs0 = phys<T>(p).cs0;
+#pragma unroll
+    for (int k = 0; k < L::NSHELL; ++k) {
+        const T dw0 = weight<LAT, T>(k, cs2) * drs +
+                      phys<T>(p).rho0 * dcs2 *
+                          (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) + T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
+        float corr;
+        p.wref[dst][k * p.N + s] = local_ref(p.pf, k, float(dw0), corr);
+    }
+}
+
+// rho = sum_i n_i of FP64 populations [Q][N] (references for imported populations)
+template <int LAT>
+__global__ void k_pops_rho(DevSim p, const double* in, double* rho)
+{
+    const long long s = gtid();
+    if (s >= p.N) return;
+    double r = 0.0;
+#pragma unroll
+    for (int i = 0; i < Lat<LAT>::Q; ++i) r += in[(long long)i * p.N + s];
+    rho[s] = r;
+}
+
+// The value of population i at site s of buffer b in the FP64 export convention (n_i itself).
+template <int LAT, int S>
+__device__ __forceinline__ double pop_full(const DevSim& p, int b, int i, long long s)
+{
+    using L = Lat<LAT>;
+    using C = Codec<S>;
+    const double v = pop_raw<LAT, S, double>(p, b, i, s);
+    if (C::LOC) {
+        // the decoded value every density sum uses: fl(stored + sender's reference) for the
+        // moving populations, the exact pair plus the own reference for the rest population
+        if (i == 0) return v + double(p.wref[b][s]);
+        const int x = int(s % p.nx), y = int((s / p.nx) % p.ny), z = int(s / ((long long)p.nx * p.ny));
+        return double(__fadd_rn(float(v), p.wref[b][L::shell(i) * p.N + sender<LAT>(p, x, y, z, i)]));
+    }
+    return v + (C::DEV ? p.off[L::shell(i)] : 0.0);
 }
 
 template <int LAT, typename T, typename U>
@@ -1572,8 +1768,7 @@ __global__ void k_pops_out(DevSim p, int src, double* out)
     const long long s = gtid();
     if (s >= p.N) return;
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i)
-        out[(long long)i * p.N + s] = pop_raw<LAT, S, double>(p, src, i, s) + (C::DEV ? p.off[L::shell(i)] : 0.0);
+    for (int i = 0; i < L::Q; ++i) out[(long long)i * p.N + s] = pop_full<LAT, S>(p, src, i, s);
 }
 
 template <int LAT, int S>
@@ -1583,9 +1778,14 @@ __global__ void k_pops_in(DevSim p, const double* in, int dst)
     using C = Codec<S>;
     const long long s = gtid();
     if (s >= p.N) return;
+    const int x = int(s % p.nx), y = int((s / p.nx) % p.ny), z = int(s / ((long long)p.nx * p.ny));
 #pragma unroll
-    for (int i = 0; i < L::Q; ++i)
-        pop_put<LAT, S, double>(p, dst, i, s, in[(long long)i * p.N + s] - (C::DEV ? p.off[L::shell(i)] : 0.0));
+    for (int i = 0; i < L::Q; ++i) {
+        // relative to the reference the decode of buffer dst will add
+        const double ref = C::LOC ? double(p.wref[dst][L::shell(i) * p.N + (i == 0 ? s : sender<LAT>(p, x, y, z, i))])
+                                  : (C::DEV ? p.off[L::shell(i)] : 0.0);
+        pop_put<LAT, S, double>(p, dst, i, s, in[(long long)i * p.N + s] - ref);
+    }
 }
 
 // FP64 sums of rho and sum_i n_i c_i: fixed grid, fixed tree, so the result is
@@ -1603,7 +1803,7 @@ __global__ void k_red_partial(DevSim p, int src, double* part)
     for (long long s = blockIdx.x * (long long)RED_BLOCK + threadIdx.x; s < p.N; s += (long long)RED_GRID * RED_BLOCK) {
 #pragma unroll
         for (int i = 0; i < L::Q; ++i) {
-            const double v = pop_raw<LAT, S, double>(p, src, i, s) + (C::DEV ? p.off[L::shell(i)] : 0.0);
+            const double v = pop_full<LAT, S>(p, src, i, s);
             acc[0] += v;
             acc[1] += L::cx(i) * v;
             acc[2] += L::cy(i) * v;
@@ -1656,6 +1856,9 @@ KernelTable make_table(bool read_pops)
     t.derivs = (const void*)k_derivs<LAT, T, U>;
     t.collide = read_pops ? (const void*)k_collide<LAT, T, S, U, true> : (const void*)k_collide<LAT, T, S, U, false>;
     t.init_eq = (const void*)k_init_eq<LAT, T, S>;
+    t.init_ref = Codec<S>::LOC ? (const void*)k_init_ref<LAT, T> : nullptr;
+    t.pops_rho = (const void*)k_pops_rho<LAT>;
+    t.local_ref = Codec<S>::LOC;
     t.fields_out = (const void*)k_fields_out<LAT, T, U>;
     t.pops_out = (const void*)k_pops_out<LAT, S>;
     t.pops_in = (const void*)k_pops_in<LAT, S>;

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_HERE, "liblbm.so")
 LBM_D2Q21, LBM_D3Q59 = 0, 1
 LBM_EOS_VDW, LBM_EOS_PSI_SINE = 0, 1
 LBM_STORE_F32, LBM_STORE_F32_DEV, LBM_STORE_F16_DEV, LBM_STORE_BF16_DEV, LBM_STORE_F64 = 0, 1, 2, 3, 4
+LBM_STORE_F32_LOC, LBM_STORE_F16_LOC, LBM_STORE_BF16_LOC = 5, 6, 7
 LBM_USOLVE_NATIVE, LBM_USOLVE_F64 = 0, 1
 LBM_OK = 0
 LBM_E_INVALID_ARG, LBM_E_WEIGHTS, LBM_E_BULKVISC, LBM_E_USOLVE_DIVERGED = -1, -2, -3, -4

@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("storage,tol", [(P.LBM_STORE_F64, 1e-13), (P.LBM_STORE_F32, 1e-12),
-                                         (P.LBM_STORE_F32_DEV, 1e-12), (P.LBM_STORE_F16_DEV, 1e-12)])
+                                         (P.LBM_STORE_F32_DEV, 1e-12), (P.LBM_STORE_F16_DEV, 1e-12),
+                                         (P.LBM_STORE_F32_LOC, 1e-12), (P.LBM_STORE_F16_LOC, 1e-12)])
 def test_mass_and_momentum_conserved(storage, tol):
     case = W.make_case("droplet3d", dims=(24, 20, 22))
     rng = np.random.default_rng(3)
@@ -31,15 +32,16 @@ def test_mass_and_momentum_conserved(storage, tol):
     assert s1.usolve_iters_last >= 1
 
 
-def test_checkpoint_resume_is_bitwise(tmp_path):
+@pytest.mark.parametrize("storage", [P.LBM_STORE_F32, P.LBM_STORE_F16_LOC])
+def test_checkpoint_resume_is_bitwise(tmp_path, storage):
     case = W.make_case("droplet2d", dims=(48, 40))
-    a = lib_sim(case, storage=P.LBM_STORE_F32)
+    a = lib_sim(case, storage=storage)
     a.init(case.rho)
     a.step(7)
     path = os.path.join(tmp_path, "ck.bin")
     a.save(path)
     a.step(9)
-    b = lib_sim(case, storage=P.LBM_STORE_F32)
+    b = lib_sim(case, storage=storage)
     b.load(path)
     b.step(9)
     assert np.array_equal(a.populations(), b.populations())
@@ -122,7 +124,7 @@ def test_usolve_cap_is_reported():
     assert st.usolve_iters_last == 3
 
 
-@pytest.mark.parametrize("storage", [P.LBM_STORE_F32_DEV, P.LBM_STORE_F16_DEV])
+@pytest.mark.parametrize("storage", [P.LBM_STORE_F32_DEV, P.LBM_STORE_F16_DEV, P.LBM_STORE_F16_LOC])
 def test_full_size_spinodal_properties(storage):
     """256^3 D3Q59 spinodal as the benchmark launches it: mass and momentum conservation,
     a finite state, a converged u-solve, and bitwise covariance under a periodic shift."""
@@ -149,3 +151,22 @@ def test_full_size_spinodal_properties(storage):
     n4 = n.view(59, 256, 256, 256)
     m4 = m.view(59, 256, 256, 256)
     assert torch.equal(torch.roll(n4, shifts=shift, dims=(1, 2, 3)), m4)
+
+
+@pytest.mark.parametrize("storage,tol", [(P.LBM_STORE_F32_DEV, 1e-7), (P.LBM_STORE_F16_LOC, 1e-4)])
+def test_populations_export_import_roundtrip(storage, tol):
+    """lbm_set_populations stores each population relative to the reference the decode adds;
+    exporting again returns the same populations up to one rounding of the storage, and the
+    run continues from them."""
+    case = W.make_case("droplet3d", dims=(16, 20, 24))
+    a = lib_sim(case, storage=storage)
+    a.init(case.rho)
+    a.step(5)
+    n = a.populations()
+    b = lib_sim(case, storage=storage)
+    b.set_populations(n)
+    m = b.populations()
+    assert np.abs(m - n).max() <= tol * np.abs(n).max()
+    assert abs(b.stats().mass - a.stats().mass) < 1e-6 * a.stats().mass
+    b.step(5)
+    assert b.stats().status == 0

@@ -109,7 +109,8 @@ def test_fp64_cold_start_usolve():
 
 
 @pytest.mark.parametrize("name,dims,nsteps", [("slab2d", (61, 47), 50), ("droplet3d", (21, 18, 23), 10)])
-@pytest.mark.parametrize("storage,tol_rho,tol_u", [(P.LBM_STORE_F32_DEV, 1e-6, 5e-4), (P.LBM_STORE_F32, 5e-6, 2e-3)])
+@pytest.mark.parametrize("storage,tol_rho,tol_u", [(P.LBM_STORE_F32_DEV, 1e-6, 5e-4), (P.LBM_STORE_F32, 5e-6, 2e-3),
+                                                   (P.LBM_STORE_F32_LOC, 1e-6, 5e-4)])
 def test_fp32_step_parity(name, dims, nsteps, storage, tol_rho, tol_u):
     case = W.make_case(name, dims=dims)
     g, o = _run_both(case, nsteps, storage=storage)
@@ -119,10 +120,13 @@ def test_fp32_step_parity(name, dims, nsteps, storage, tol_rho, tol_u):
     assert u_err(u_g, u_o, o.cs0) < tol_u
 
 
-@pytest.mark.parametrize("storage,tol_rho", [(P.LBM_STORE_F16_DEV, 5e-4), (P.LBM_STORE_BF16_DEV, 3e-3)])
+@pytest.mark.parametrize("storage,tol_rho", [(P.LBM_STORE_F16_DEV, 5e-4), (P.LBM_STORE_BF16_DEV, 3e-3),
+                                             (P.LBM_STORE_F16_LOC, 2e-5), (P.LBM_STORE_BF16_LOC, 2e-4)])
 def test_reduced_precision_storage_error(storage, tol_rho):
-    """16-bit deviations: rounding 2^-11 (FP16) or 2^-8 (BF16) of |n_i - w_i(rho0) rho0| per step;
-    the FP32 rest plane keeps mass exact, so the error stays bounded instead of drifting."""
+    """16-bit deviations: rounding 2^-11 (FP16) or 2^-8 (BF16) of the stored deviation per step:
+    |n_i - w_i(rho0) rho0| (10-20 % of n_i across the phases) for the global reference, only the
+    velocity and non-equilibrium parts for the sender's local reference.  The FP32 rest plane
+    keeps mass exact, so the error stays bounded instead of drifting."""
     case = W.make_case("droplet2d", dims=(64, 52))
     g, o = _run_both(case, 20, storage=storage)
     rho_g, _ = g.fields()
@@ -163,3 +167,20 @@ def test_slab_1000_steps_fp64_and_fp32():
         rho_g, u_g = g.fields()
         assert rel_linf(rho_g, rho_o) < tol_rho
         assert u_err(u_g, u_o, o.cs0) < tol_u
+
+
+@pytest.mark.parametrize("storage,tol", [(P.LBM_STORE_F32_LOC, 1e-7), (P.LBM_STORE_F16_LOC, 1e-4),
+                                         (P.LBM_STORE_BF16_LOC, 1e-3)])
+@pytest.mark.parametrize("name,dims", [("droplet2d", (64, 52)), ("droplet3d", (21, 18, 23))])
+def test_local_reference_initial_populations(storage, tol, name, dims):
+    """The initial populations through the senders' references: each stored deviation plus the
+    reference of the site at -c_i decodes to n^eq of the site (the rest population closes the
+    mass exactly, so it carries the others' rounding).  FP32: the float evaluation of
+    X = (c.u)/cs2 + ... (about 2e-7 of X with this flow) bounds the error, as for the other
+    FP32 storages; 16-bit: the storage's rounding of the deviations."""
+    case = W.make_case(name, dims=dims)
+    rng = np.random.default_rng(2)
+    case.u = 0.02 * rng.standard_normal((len(dims),) + case.rho.shape)
+    g, o = _run_both(case, 0, storage=storage)
+    idx = perm_to_oracle(case.lattice)
+    assert rel_linf(g.populations()[idx], o.pops()) < tol
