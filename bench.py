@@ -311,16 +311,19 @@ def run_native(args):
                          "frac": step_gbs / peak}}
 
     # the FP16-deviation storage form of the same workload
+    # the 16-bit storage forms of the same workload: deviations from w_i(rho0) rho0, and from the
+    # sender's local w_i(rho) rho (error against FP64: see the configuration tests)
     extra = {}
     if args.storage in ("f32", "f32dev") and not args.no_extras:
         del sim
         torch.cuda.empty_cache()
-        sim16 = make_sim(STORAGES["f16dev"])
-        ms16, _, sweeps16, _ = timed(sim16, K, Wm)
-        extra["fp16_dev_storage"] = {"value": whole_job_mlups(ws, N, K, ms16 / 1e3), "unit": UNIT,
-                                     "speedup_vs_f32": ms / ms16, "ms_per_step": ms16 / K}
-        del sim16
-        torch.cuda.empty_cache()
+        for key, st in (("fp16_dev_storage", "f16dev"), ("fp16_local_storage", "f16loc")):
+            sim16 = make_sim(STORAGES[st])
+            ms16, _, sweeps16, _ = timed(sim16, K, Wm)
+            extra[key] = {"value": whole_job_mlups(ws, N, K, ms16 / 1e3), "unit": UNIT, "speedup_vs_f32": ms / ms16,
+                          "ms_per_step": ms16 / K, "usolve_sweeps_per_step": sweeps16 / K}
+            del sim16
+            torch.cuda.empty_cache()
         sim = make_sim(storage)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region

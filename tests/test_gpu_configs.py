@@ -104,8 +104,11 @@ def test_config_droplet3d_128_storages_vs_fp64_2000_steps():
     # the 16-bit storages round the deviation from w_i(rho0) rho0, about 10-20 % of n_i across the
     # two phases, to 2^-11 (half) or 2^-8 (bfloat16) each step; measured after 2000 steps:
     # 1.6e-3 (half) and 7.6e-3 (bfloat16); the bounds allow a factor of 2
+    # with the sender's local reference only the velocity and non-equilibrium parts are rounded:
+    # measured 3.8e-6 (half) and 4.2e-4 (bfloat16)
     for name, st, tol in (("fp32dev", P.LBM_STORE_F32_DEV, 1e-6), ("fp16dev", P.LBM_STORE_F16_DEV, 3e-3),
-                          ("bf16dev", P.LBM_STORE_BF16_DEV, 1.5e-2)):
+                          ("bf16dev", P.LBM_STORE_BF16_DEV, 1.5e-2), ("fp32loc", P.LBM_STORE_F32_LOC, 1e-6),
+                          ("fp16loc", P.LBM_STORE_F16_LOC, 1e-5), ("bf16loc", P.LBM_STORE_BF16_LOC, 1e-3)):
         r, u, _ = _run(case, 2000, st)
         out[name + "_rho_rel_linf"] = rel_linf(r, r64)
         out[name + "_u_err"] = u_err(u, u64, cs0)
