@@ -457,9 +457,16 @@ __global__ void __launch_bounds__(256, 3) k_moments(DevSim p, int src, int pair)
         for (int i = C::EXACT ? 1 : 0; i < L::Q; ++i) {
             if (C::EXACT) acc2(hi, lo, float(v[i]));
             else sum += v[i];
-            if (L::cx(i)) j[0] += T(L::cx(i)) * v[i];
-            if (L::cy(i)) j[1] += T(L::cy(i)) * v[i];
-            if (L::cz(i)) j[2] += T(L::cz(i)) * v[i];
+        }
+        // j0 over opposite pairs: c_i (n_i - n_-i), whose difference is exact for nearly equal
+        // populations and whose products with c in {1, 2, 4} are exact, so the partial sums stay
+        // at the size of j0 instead of the size of the populations
+#pragma unroll
+        for (int i = 1; i < L::Q; i += 2) {
+            const T d = v[i] - v[i + 1];
+            if (L::cx(i)) j[0] += T(L::cx(i)) * d;
+            if (L::cy(i)) j[1] += T(L::cy(i)) * d;
+            if (L::cz(i)) j[2] += T(L::cz(i)) * d;
         }
     }
     // rho - rho0: the deviation sum itself (sum_i w_i(rho0) rho0 = rho0 and the
@@ -1408,10 +1415,14 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
                     const T rho = phys<T>(p).rho0 + pr[m];
 #pragma unroll
                     for (int a = 0; a < 3; ++a) dst[a * RY * RX + k] = a < D ? T(pt[m][a]) : T(0);
-                    const T P = eos_p<T>(p, rho);
+                    // p and p/rho as deviations from their values at rho0, from the difference
+                    // formula: the derivative stencils (weights summing to zero) see the same
+                    // differences without the rounding of the O(1) offsets
+                    T cs2, dcs2;
+                    cs2_delta<T>(p, pr[m], cs2, dcs2);
                     dst[3 * RY * RX + k] = rho;
-                    dst[4 * RY * RX + k] = P;
-                    dst[5 * RY * RX + k] = P / rho;
+                    dst[4 * RY * RX + k] = phys<T>(p).rho0 * dcs2 + pr[m] * cs2;  // p - p(rho0)
+                    dst[5 * RY * RX + k] = dcs2;                                   // p/rho - c_s^2(rho0)
                 }
             }
             if (zl + 1 < z1 + HZ) fetch(zl + 1);
@@ -1428,6 +1439,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
         if (zc >= z0 && zc < z1) {
             const int gz = D == 3 ? zc : 0;
             const T* pl[5];
+            const T p0 = phys<T>(p).rho0 * phys<T>(p).cs0;  // p(rho0)
             ring_planes<D, T>(sr, NP * RY * RX, zc, pl);
             constexpr int PS = RY * RX;
             for (int k = tid; k < TX * TY; k += nth) {
@@ -1450,7 +1462,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
 #pragma unroll
                         for (int c = b; c < D; ++c)
                             dpuu[a][b][c] = d1p<T>(pl, a, ri, RX, [&](const T* P, int j) {
-                                return P[4 * PS + j] * P[b * PS + j] * P[c * PS + j];
+                                return (p0 + P[4 * PS + j]) * P[b * PS + j] * P[c * PS + j];
                             });
                 }
                 const long long s = at(p, gx, gy, gz);
