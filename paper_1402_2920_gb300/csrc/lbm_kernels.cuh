@@ -764,25 +764,24 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
         const int c[3] = {cx, cy, cz};
         const int k = L::shell(i);
-        // shell constants (pure in k: shared by the shell's pairs)
-        const T wl = weight<LAT, T>(k, cs2);
-        const T wr = wl * rs;
+        // shell constants (pure in k: shared by the shell's pairs).  w(s) = w(s0) + (s - s0) [c1 +
+        // c2 (s + s0) + c3 (s^2 + s s0 + s0^2)]: the difference form keeps the relative accuracy of
+        // the outer shells' small weights, which the cubic itself would lose to cancellation
         const T w0k = q.w0[k];
+        const T dwk = dcs2 * (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) +
+                              T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
+        const T wl = w0k + dwk;
+        const T wr = wl * rs;
         T even0;
         float lref = 0.f, lcorr = 0.f;  // this site's reference for shell k and w rho - reference
         if (C::LOC) {
             // n^eq - w rho = w rho X; the stored value is relative to the float reference
-            const T dw0 = wl * drs + q.rho0 * dcs2 *
-                                         (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) +
-                                          T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
+            const T dw0 = wl * drs + q.rho0 * dwk;
             lref = local_ref(p.pf, k, float(dw0), lcorr);
             even0 = omg * (wr * B1) + w0k * q.cf_h2 * h2c + T(lcorr);
         } else if (C::DEV) {
-            // n^eq - w(rho0) rho0 = w rho X + w drho + rho0 (w(s) - w(s0)), with
-            // w(s) - w(s0) = (s - s0) [c1 + c2 (s + s0) + c3 (s^2 + s s0 + s0^2)]
-            const T dw0 = wl * drs + q.rho0 * dcs2 *
-                                         (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) +
-                                          T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
+            // n^eq - w(rho0) rho0 = w rho X + w drho + rho0 (w(s) - w(s0))
+            const T dw0 = wl * drs + q.rho0 * dwk;
             even0 = omg * (wr * B1 + dw0) + w0k * q.cf_h2 * h2c;
         } else {
             even0 = omg * wr * (T(1) + B1) + w0k * q.cf_h2 * h2c;
@@ -842,10 +841,9 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
         float* wf = p.wref[src ^ 1];
 #pragma unroll
         for (int k = 0; k < L::NSHELL; ++k) {
-            const T wl = weight<LAT, T>(k, cs2);
-            const T dw0 = wl * drs + q.rho0 * dcs2 *
-                                         (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) +
-                                          T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
+            const T dwk = dcs2 * (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) +
+                                  T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
+            const T dw0 = (q.w0[k] + dwk) * drs + q.rho0 * dwk;
             float corr;
             const float wk = local_ref(p.pf, k, float(dw0), corr);
             wf[k * p.N + s] = wk;
@@ -1690,10 +1688,11 @@ __global__ void k_init_eq(DevSim p, const double* rho_in, const double* u_in, in
         const T w = weight<LAT, T>(k, cs2);
         if (C::LOC) {
             // as if sent by the neighbour at -c_i: n^eq here minus that site's reference, in FP64
-            const double ref = double(wf[k * p.N + sender<LAT>(p, x, y, z, i)]);
+            const float ref = wf[k * p.N + sender<LAT>(p, x, y, z, i)];
             const double wd = lat_weight_d<LAT>(k, p, rho_in[s]) * rho_in[s];
-            const double dev = (wd - ref) + wd * double(X);
-            stored_sum += double(pop_put<LAT, S, double>(p, dst, i, s, dev)) + ref;
+            const double dev = (wd - double(ref)) + wd * double(X);
+            // the decoded float the moments kernel will sum
+            stored_sum += double(__fadd_rn(float(pop_put<LAT, S, double>(p, dst, i, s, dev)), ref));
             continue;
         }
         const T dev = w * rs * X + w * drs +
