@@ -89,8 +89,9 @@ typedef struct {
     int storage;           /* LBM_STORE_*                                                 */
     int usolve_precision;  /* LBM_USOLVE_*                                                */
     double usolve_tol;     /* stop when max|j~new - j~| <= usolve_tol + usolve_rtol max|j~new|;
-                              both <= 0 select the default of the arithmetic: 1e-14 for FP64,
-                              5e-9 for FP32 (about 20 times below the FP32 rounding of u)   */
+                              both <= 0 select the default: 1e-14 for an FP64 u-solve; else
+                              5e-9 (32-bit storages) or 4e-8 (16-bit storages), below the
+                              rounding noise the stored populations put into j0 each step   */
     double usolve_rtol;
     int usolve_max_iter;   /* sweep cap per u-solve; <= 0 selects 500                     */
     int usolve_warm_start; /* 1: start from the previous step's j~ (Sec. IX item 3); 0: from 0 (S1) */
