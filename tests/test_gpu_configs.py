@@ -81,9 +81,9 @@ def test_config_droplet2d_512_fp32_vs_fp64_5000_steps():
             fp32dev_u_err=e_u, fp32dev_rho_rel_linf_1000=e_rho_1k, fp32dev_u_err_1000=e_u_1k, laplace_dp=dp,
             laplace_sigma_over_R=dp_pred, radius=R, max_spurious_u=float(np.abs(u64).max()),
             mass_drift_fp32=abs(s32.mass - s64.mass) / s64.mass)
-    # FP32 storage rounds each deviation to 2^-24 of itself every step; on a nearly static state
-    # the rounding repeats, so the error grows about linearly: ~1.5e-6 per 1000 steps here
-    assert e_rho_1k < 2e-6 and e_rho < 1e-5
+    # FP32: the collision's arithmetic rounding repeats on a nearly static state, so the error
+    # grows about linearly: 5.5e-7 after 1000 steps, 3.4e-6 after 5000
+    assert e_rho_1k < 1e-6 and e_rho < 1e-5
     # the velocity is the spurious current (~1e-4); the FP32 rounding of j0 = sum n_i c_i
     # (~3e-7 absolute) sets the floor of e_u on the scale max(|u|, 1e-3 c_s)
     assert e_u < 1e-3
@@ -105,9 +105,12 @@ def test_config_droplet3d_128_storages_vs_fp64_2000_steps():
     # two phases, to 2^-11 (half) or 2^-8 (bfloat16) each step; measured after 2000 steps:
     # 1.6e-3 (half) and 7.6e-3 (bfloat16); the bounds allow a factor of 2
     # with the sender's local reference only the velocity and non-equilibrium parts are rounded:
-    # measured 3.8e-6 (half) and 4.2e-4 (bfloat16)
-    for name, st, tol in (("fp32dev", P.LBM_STORE_F32_DEV, 1e-6), ("fp16dev", P.LBM_STORE_F16_DEV, 3e-3),
-                          ("bf16dev", P.LBM_STORE_BF16_DEV, 1.5e-2), ("fp32loc", P.LBM_STORE_F32_LOC, 1e-6),
+    # measured 3.0e-6 (half) and 4.0e-4 (bfloat16).  FP32: 3.1e-6 after 2000 steps, set by the
+    # FP32 arithmetic of the collision (every storage shows it); its size depends on rounding
+    # details (the cubic weight polynomial instead of its difference form gives 4e-7 here and
+    # 1.5e-6 instead of 5.5e-7 on the 512^2 droplet after 1000 steps)
+    for name, st, tol in (("fp32dev", P.LBM_STORE_F32_DEV, 5e-6), ("fp16dev", P.LBM_STORE_F16_DEV, 3e-3),
+                          ("bf16dev", P.LBM_STORE_BF16_DEV, 1.5e-2), ("fp32loc", P.LBM_STORE_F32_LOC, 5e-6),
                           ("fp16loc", P.LBM_STORE_F16_LOC, 1e-5), ("bf16loc", P.LBM_STORE_BF16_LOC, 1e-3)):
         r, u, _ = _run(case, 2000, st)
         out[name + "_rho_rel_linf"] = rel_linf(r, r64)
