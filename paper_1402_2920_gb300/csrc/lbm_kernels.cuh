@@ -18,6 +18,7 @@
 #include <cuda_fp16.h>
 
 #include <type_traits>
+#include <utility>
 
 #include "lbm_common.h"
 #include "lbm_lattice.h"
@@ -691,6 +692,53 @@ __host__ __device__ constexpr int shell_count(int k)
     return m;
 }
 
+// Pair (odd index) whose first velocity is +- m c_i: its index, negative when it is -m c_i; 0 if
+// no pair has it.
+template <int LAT>
+__host__ __device__ constexpr int pair_multiple(int i, int m)
+{
+    using L = Lat<LAT>;
+    for (int j = 1; j < L::Q; j += 2) {
+        if (L::cx(j) == m * L::cx(i) && L::cy(j) == m * L::cy(i) && L::cz(j) == m * L::cz(i)) return j;
+        if (L::cx(j) == -m * L::cx(i) && L::cy(j) == -m * L::cy(i) && L::cz(j) == -m * L::cz(i)) return -j;
+    }
+    return 0;
+}
+
+// Lowest pair index of shell k (0 for the rest shell).
+template <int LAT>
+__host__ __device__ constexpr int first_pair_of_shell(int k)
+{
+    for (int i = 1; i < Lat<LAT>::Q; i += 2)
+        if (Lat<LAT>::shell(i) == k) return i;
+    return 0;
+}
+
+// A pair is a base pair unless its velocity is 2 or 4 times another pair's.
+template <int LAT>
+__host__ __device__ constexpr bool pair_base(int i)
+{
+    using L = Lat<LAT>;
+    for (int j = 1; j < L::Q; j += 2)
+        for (int m = 2; m <= 4; m *= 2) {
+            const int q = pair_multiple<LAT>(j, m);
+            if (q == i || q == -i) return false;
+        }
+    return true;
+}
+
+// f(integral_constant<int, 0>), ..., f(integral_constant<int, N - 1>) at compile time
+template <int... I, class F>
+__device__ __forceinline__ void static_foreach_impl(std::integer_sequence<int, I...>, F&& f)
+{
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void static_foreach(F&& f)
+{
+    static_foreach_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
 // i and i + 1 are opposite velocities for every odd i (the tables' order)
 template <int LAT>
 __host__ __device__ constexpr bool pairs_opposite()
@@ -759,10 +807,10 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
     // (sum_i Delta_i = 0 holds exactly for the method's collision operator).
     T stored_sum = T(0);
     float sh = 0.f, sl = 0.f;  // float-pair sum of the stored values (EXACT storages)
-#pragma unroll
-    for (int i = 1; i < L::Q; i += 2) {
+    // One pair of opposite velocities (i, i + 1) from its contractions c.u, c.V, Sigma:cc, Xi':ccc.
+    auto emit = [&](auto ic, T uc, T lin, T h2, T h3) {
+        constexpr int i = decltype(ic)::value;
         const int cx = L::cx(i), cy = L::cy(i), cz = L::cz(i);
-        const int c[3] = {cx, cy, cz};
         const int k = L::shell(i);
         // shell constants (pure in k: shared by the shell's pairs).  w(s) = w(s0) + (s - s0) [c1 +
         // c2 (s + s0) + c3 (s^2 + s s0 + s0^2)]: the difference form keeps the relative accuracy of
@@ -779,6 +827,8 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
             const T dw0 = wl * drs + q.rho0 * dwk;
             lref = local_ref(p.pf, k, float(dw0), lcorr);
             even0 = omg * (wr * B1) + w0k * q.cf_h2 * h2c + T(lcorr);
+            // the reference the decoder adds is this very value (one store per shell)
+            if (i == first_pair_of_shell<LAT>(k)) p.wref[src ^ 1][k * p.N + s] = lref;
         } else if (C::DEV) {
             // n^eq - w(rho0) rho0 = w rho X + w drho + rho0 (w(s) - w(s0))
             const T dw0 = wl * drs + q.rho0 * dwk;
@@ -786,26 +836,6 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
         } else {
             even0 = omg * wr * (T(1) + B1) + w0k * q.cf_h2 * h2c;
         }
-        // the pair's c-dependent parts
-        T uc = T(0), lin = T(0), h2 = T(0), h3 = T(0);
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-            if (c[a]) { uc += T(c[a]) * u[a]; lin += T(c[a]) * V[a]; }
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-#pragma unroll
-            for (int b = a; b < D; ++b)
-                if (c[a] && c[b]) h2 += T((a == b ? 1 : 2) * c[a] * c[b]) * Sig[a][b];
-#pragma unroll
-        for (int a = 0; a < D; ++a)
-#pragma unroll
-            for (int b = a; b < D; ++b)
-#pragma unroll
-                for (int e = b; e < D; ++e)
-                    if (c[a] && c[b] && c[e]) {
-                        const int mult = (a == b && b == e) ? 1 : (a == b || b == e) ? 3 : 6;
-                        h3 += T(mult * c[a] * c[b] * c[e]) * Xi[sym3<D>(a, b, e)];
-                    }
         const T E = omg * wr * A1 * uc * uc + w0k * q.cf_h2 * h2 + even0;
         const T O = omg * wr * ics2 * uc + w0k * (lin + q.cf_h3 * h3);
         T np = E + O, nm = E - O;
@@ -834,21 +864,56 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
             stored_sum += sp;
             stored_sum += sm;
         }
-    }
-    if (C::LOC) {
-        // this site's references for the populations it sends; the rest population's own
-        // reference joins the float pair (the others are inside the decoded values)
-        float* wf = p.wref[src ^ 1];
+    };
+    // The contractions of the base pairs; a pair whose velocity is m c of a base pair (m = 2, 4)
+    // takes them scaled by m, m, m^2, m^3, which is exact in floating point (m a power of two).
+    static_foreach<(L::Q - 1) / 2>([&](auto pc) {
+        constexpr int i = 2 * decltype(pc)::value + 1;
+        if constexpr (pair_base<LAT>(i)) {
+            const int c[3] = {L::cx(i), L::cy(i), L::cz(i)};
+            T uc = T(0), lin = T(0), h2 = T(0), h3 = T(0);
 #pragma unroll
-        for (int k = 0; k < L::NSHELL; ++k) {
-            const T dwk = dcs2 * (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) +
-                                  T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
-            const T dw0 = (q.w0[k] + dwk) * drs + q.rho0 * dwk;
-            float corr;
-            const float wk = local_ref(p.pf, k, float(dw0), corr);
-            wf[k * p.N + s] = wk;
-            if (k == 0) acc2(sh, sl, wk);
+            for (int a = 0; a < D; ++a)
+                if (c[a]) { uc += T(c[a]) * u[a]; lin += T(c[a]) * V[a]; }
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = a; b < D; ++b)
+                    if (c[a] && c[b]) h2 += T((a == b ? 1 : 2) * c[a] * c[b]) * Sig[a][b];
+#pragma unroll
+            for (int a = 0; a < D; ++a)
+#pragma unroll
+                for (int b = a; b < D; ++b)
+#pragma unroll
+                    for (int e = b; e < D; ++e)
+                        if (c[a] && c[b] && c[e]) {
+                            const int mult = (a == b && b == e) ? 1 : (a == b || b == e) ? 3 : 6;
+                            h3 += T(mult * c[a] * c[b] * c[e]) * Xi[sym3<D>(a, b, e)];
+                        }
+            emit(std::integral_constant<int, i>{}, uc, lin, h2, h3);
+            constexpr int j2 = pair_multiple<LAT>(i, 2), j4 = pair_multiple<LAT>(i, 4);
+            if constexpr (j2 != 0) {
+                constexpr int jp = j2 > 0 ? j2 : -j2;
+                const T sg = T(j2 > 0 ? 1 : -1);
+                emit(std::integral_constant<int, jp>{}, sg * T(2) * uc, sg * T(2) * lin, T(4) * h2, sg * T(8) * h3);
+            }
+            if constexpr (j4 != 0) {
+                constexpr int jp = j4 > 0 ? j4 : -j4;
+                const T sg = T(j4 > 0 ? 1 : -1);
+                emit(std::integral_constant<int, jp>{}, sg * T(4) * uc, sg * T(4) * lin, T(16) * h2, sg * T(64) * h3);
+            }
         }
+    });
+    if (C::LOC) {
+        // the rest population's reference (shell 0, no pair): it joins the float pair, the others
+        // are inside the decoded values
+        const T dwk = dcs2 * (T(L::wc(0, 1)) + T(L::wc(0, 2)) * (cs2 + cs0) +
+                              T(L::wc(0, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
+        const T dw0 = (q.w0[0] + dwk) * drs + q.rho0 * dwk;
+        float corr;
+        const float wk = local_ref(p.pf, 0, float(dw0), corr);
+        p.wref[src ^ 1][s] = wk;
+        acc2(sh, sl, wk);
     }
     // rest population: the stored convention sums to rho - rho0 (global deviations) or rho
     if (C::EXACT) {

@@ -53,3 +53,29 @@ def test_no_cpu_fallback_without_gpu(lib):
     with pytest.raises(P.LbmError) as e:
         P.Sim(P.LBM_D2Q21, (16, 16), eos, P.make_params(kappa=0.05))
     assert e.value.code == P.LBM_E_CUDA
+
+
+def test_velocity_pairs_are_bases_or_power_of_two_multiples(lib):
+    """The collision computes the contractions of a pair of opposite velocities once per base
+    pair and scales them for the pairs whose velocity is 2 or 4 times a base velocity: every pair
+    must be exactly one of the two."""
+    for lat, bases in ((P.LBM_D2Q21, 4), (P.LBM_D3Q59, 13)):
+        c = P.lbm_velocities(lat)
+        q = len(c)
+
+        def multiple(i, m):
+            for j in range(1, q, 2):
+                if (c[j] == m * c[i]).all() or (c[j] == -m * c[i]).all():
+                    return j
+            return 0
+
+        derived = {multiple(j, m) for j in range(1, q, 2) for m in (2, 4)} - {0}
+        base = [i for i in range(1, q, 2) if i not in derived]
+        assert len(base) == bases
+        count = {j: 0 for j in range(1, q, 2)}
+        for i in base:
+            count[i] += 1
+            for m in (2, 4):
+                if multiple(i, m):
+                    count[multiple(i, m)] += 1
+        assert all(v == 1 for v in count.values())
