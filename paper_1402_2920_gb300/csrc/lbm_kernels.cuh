@@ -66,8 +66,9 @@ struct Codec<ST_F32> {
     static constexpr bool DEV = false, SPLIT0 = true, EXACT = true, SCALED = false, LOC = false;
     template <typename T>
     __device__ static T raw(const type* p, long long k) { return T(p[k]); }
+    // evict-first: the populations are read again only in the next step, long after L2 turned over
     template <typename T>
-    __device__ static void put(type* p, long long k, T v) { p[k] = float(v); }
+    __device__ static void put(type* p, long long k, T v) { __stcs(p + k, float(v)); }
     template <typename T>
     __device__ static T rounded(T v) { return T(float(v)); }
 };
@@ -78,7 +79,7 @@ struct Codec<ST_F32_DEV> {
     template <typename T>
     __device__ static T raw(const type* p, long long k) { return T(p[k]); }
     template <typename T>
-    __device__ static void put(type* p, long long k, T v) { p[k] = float(v); }
+    __device__ static void put(type* p, long long k, T v) { __stcs(p + k, float(v)); }
     template <typename T>
     __device__ static T rounded(T v) { return T(float(v)); }
 };
