@@ -945,29 +945,22 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
 template <int D>
 struct Tile {
     static constexpr int TX = 32, TY = D == 3 ? 8 : 16, ZB = D == 3 ? 32 : 1;
-    static constexpr int NZR = D == 3 ? 5 : 1;
     static constexpr int THREADS = TX * TY;
 };
 
-template <int D>
-__device__ __forceinline__ int ring_slot(int z)
-{
-    return D == 3 ? (z + 40) % 5 : 0;
-}
-
-// Base pointers of the ring planes z-2 .. z+2 (D = 3) or of the single plane (D = 2).
+// Ring of the derivative kernel: the 5 planes of the stencil, plus (FP32) one more, so that the
+// slot written next never holds a plane the previous pass still reads (one barrier per plane).
 template <int D, typename T>
-__device__ __forceinline__ void ring_planes(T* ring, int plane_elems, int z, const T* (&pl)[5])
-{
-    if (D == 3) {
-        const int s0 = (z + 38) % 5;  // slot of plane z - 2 (z >= -8)
+struct DerivsPlan {
+    static constexpr int R = D == 3 ? (sizeof(T) == 4 ? 6 : 5) : 1;
+    static constexpr bool CLOSING_BARRIER = R < 6;
+    __device__ static int slot(int z) { return D == 3 ? (z + 8 * R) % R : 0; }  // z >= -8
+    __device__ static void planes(T* ring, int plane_elems, int z, const T* (&pl)[5])
+    {
 #pragma unroll
-        for (int k = 0; k < 5; ++k) pl[k] = ring + ((s0 + k) % 5) * plane_elems;
-    } else {
-#pragma unroll
-        for (int k = 0; k < 5; ++k) pl[k] = ring;
+        for (int k = 0; k < 5; ++k) pl[k] = ring + slot(D == 3 ? z - 2 + k : 0) * plane_elems;
     }
-}
+};
 
 // First derivative of Sec. IV.B along axis a, (2/3)(g(+1) - g(-1)) - (1/12)(g(+2) - g(-2)),
 // of a field read by g(plane, index) at in-plane index i (row pitch PX) of the centre plane.
@@ -1380,12 +1373,18 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_force(DevSim p, 
     }
     fetch_own(z0);
     for (int zl = z0 - HZ; zl < z1 + HZ; ++zl) {
-        // the slot of plane zl + PF held plane zl + PF - R, last read before the previous
-        // step's closing barrier
-        if (zl + PF < z1 + HZ) fetch(zl + PF);
-        cp_async_commit();
-        cp_async_wait<PF>();
-        __syncthreads();
+        if (PF == 0) {  // 2D: the single plane, in this one pass
+            fetch(zl);
+            cp_async_commit();
+        }
+        cp_async_wait<PF == 0 ? 0 : PF - 1>();  // plane zl has landed (this thread's copies)
+        __syncthreads();                         // ... and everyone's; the previous pass's reads are done
+        // The slot of plane zl + PF held plane zl + PF - R = zl - 5, which only the previous
+        // pass read, so one barrier per plane suffices.
+        if (PF > 0) {
+            if (zl + PF < z1 + HZ) fetch(zl + PF);
+            cp_async_commit();
+        }
         const int zc = zl - HZ;
         if (own && zc >= z0 && zc < z1) {
             const T* pl[5];
@@ -1421,7 +1420,6 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_force(DevSim p, 
             }
         }
         if (zc >= z0 && zc < z1) fetch_own(zc + 1);
-        __syncthreads();
     }
 }
 
@@ -1438,7 +1436,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
     constexpr int RX = TX + 4, RY = TY + 4, NP = 6;  // u_x, u_y, u_z, rho, p, p/rho
     constexpr int HZ = D == 3 ? 2 : 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* sr = reinterpret_cast<T*>(smem_raw);  // [NZR][NP][RY][RX]
+    T* sr = reinterpret_cast<T*>(smem_raw);  // [R][NP][RY][RX]
     const int tid = threadIdx.x, nth = blockDim.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
@@ -1471,7 +1469,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
     fetch(z0 - HZ);
     for (int zl = z0 - HZ; zl < z1 + HZ; ++zl) {
         {
-            T* dst = sr + ring_slot<D>(zl) * NP * RY * RX;
+            T* dst = sr + DerivsPlan<D, T>::slot(zl) * NP * RY * RX;
 #pragma unroll
             for (int m = 0; m < MR; ++m) {
                 const int k = tid + m * nth;
@@ -1504,7 +1502,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
             const int gz = D == 3 ? zc : 0;
             const T* pl[5];
             const T p0 = phys<T>(p).rho0 * phys<T>(p).cs0;  // p(rho0)
-            ring_planes<D, T>(sr, NP * RY * RX, zc, pl);
+            DerivsPlan<D, T>::planes(sr, NP * RY * RX, zc, pl);
             constexpr int PS = RY * RX;
             for (int k = tid; k < TX * TY; k += nth) {
                 const int ix = k % TX, iy = k / TX;
@@ -1538,7 +1536,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
                 derivs_tail<LAT, T>(p, s, du, divj, dp, dpr, dpuu, rs, u, jtl);
             }
         }
-        __syncthreads();
+        if (DerivsPlan<D, T>::CLOSING_BARRIER) __syncthreads();
     }
 }
 
@@ -1622,14 +1620,42 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
         fetch(z0 - HZ + k);
         cp_async_commit();
     }
+    // the thread's site in the tile (one site per thread)
+    const int ix = tid % TX, iy = tid / TX;
+    const int gx = x0 + ix, gy = y0 + iy;
     for (int zl = z0 - HZ; zl < z1 + HZ; ++zl) {
-        // the slot of plane zl + PF held plane zl + PF - R, last read before the previous
-        // step's closing barrier
-        if (zl + PF < z1 + HZ) fetch(zl + PF);
-        cp_async_commit();
-        cp_async_wait<PF>();
-        __syncthreads();
         const int zc = zl - HZ;
+        const int gz = D == 3 ? zc : 0;
+        const bool act = zc >= z0 && zc < z1 && gx < p.nx && gy < p.ny;
+        // The site's own inputs are loaded before the barrier, so their latency overlaps the
+        // wait for the ring; nothing else is live here.
+        const long long s = act ? at(p, gx, gy, gz) : 0;
+        T drs = T(0), j0s[3] = {T(0), T(0), T(0)}, f[3] = {T(0), T(0), T(0)};
+        U ua[3] = {U(0), U(0), U(0)};
+        T sigl[6];
+        if (act) {
+            drs = drho[s];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+                ua[a] = uu[a * p.N + s];
+                j0s[a] = j0p[a * p.N + s];
+                f[a] = fp[a * p.N + s];
+            }
+#pragma unroll
+            for (int q = 0; q < AL::NB; ++q) sigl[q] = aux[(AL::SIGL + q) * p.N + s];
+        }
+        if (PF == 0) {  // 2D: the single plane, in this one pass
+            fetch(zl);
+            cp_async_commit();
+        }
+        cp_async_wait<0>();  // plane zl has landed (this thread's copies)
+        __syncthreads();     // ... and everyone's; the previous pass's reads are done
+        // The slot of plane zl + PF held plane zl + PF - R = zl - 5, which only the previous
+        // pass read, so one barrier per plane suffices.
+        if (PF > 0) {
+            if (zl + PF < z1 + HZ) fetch(zl + PF);
+            cp_async_commit();
+        }
         if (zc + kCollideLead >= z0 && zc + kCollideLead < z1 && tid < TX * TY) {
             // the per-site inputs of a plane ahead, into L2 while this plane computes
             const int gx = min(x0 + tid % TX, p.nx - 1), gy = min(y0 + tid / TX, p.ny - 1);
@@ -1645,30 +1671,22 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
             prefetch_l2(drho + sn);
             if (Codec<S>::EXACT) prefetch_l2(cp<float>(p.rho_lo) + sn);
         }
-        if (zc >= z0 && zc < z1) {
-            const int gz = D == 3 ? zc : 0;
+        if (act) {
             const T* pl[5];
             CollidePlan<D>::planes(sr, NP * RY * RX, zc, pl);
             constexpr int PS = RY * RX;
-            for (int k = tid; k < TX * TY; k += nth) {
-                const int ix = k % TX, iy = k / TX;
-                const int gx = x0 + ix, gy = y0 + iy;
-                if (gx >= p.nx || gy >= p.ny) continue;
+            {
                 const int ri = (iy + 2) * RX + ix + 2;
                 Site r;
-                r.x = gx; r.y = gy; r.z = gz; r.s = at(p, gx, gy, gz);
-                const long long s = r.s;
-                const T drs = drho[s];
+                r.x = gx; r.y = gy; r.z = gz; r.s = s;
                 const T rs = phys<T>(p).rho0 + drs;
-                T u[3] = {T(0), T(0), T(0)}, f[3] = {T(0), T(0), T(0)}, jtl[3] = {T(0), T(0), T(0)};
+                T u[3] = {T(0), T(0), T(0)}, jtl[3] = {T(0), T(0), T(0)};
 #pragma unroll
                 for (int a = 0; a < D; ++a) {
-                    const U ua = uu[a * p.N + s];
-                    u[a] = T(ua);
-                    const U jta = U(rs) * ua - U(j0p[a * p.N + s]);  // j~ = rho u - j0' (S8)
+                    u[a] = T(ua[a]);
+                    const U jta = U(rs) * ua[a] - U(j0s[a]);  // j~ = rho u - j0' (S8)
                     jtl[a] = T(jta);
                     jw[a * p.N + s] = jta;  // the next step's warm start
-                    f[a] = fp[a * p.N + s];
                 }
                 T P, DP, PM, RPP;
                 eos_full<T>(p, rs, P, DP, PM, RPP);
@@ -1697,7 +1715,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
                     for (int b = a; b < D; ++b) {
                         T v = k1 * (u[a] * (dA[b] + divB[b]) + u[b] * (dA[a] + divB[a]));
                         v += k2 * (-P * (dC[a][b] + dC[b][a]) - (a == b ? PM * trdC : T(0)));
-                        v += aux[(AL::SIGL + sym2<D>(a, b)) * p.N + s];
+                        v += sigl[sym2<D>(a, b)];
                         Sig[a][b] = v;
                         Sig[b][a] = v;
                     }
@@ -1707,7 +1725,6 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
                 collide_tail<LAT, T, S, READ>(p, src, r, drs, u, f, jtl, Sig, Xi);
             }
         }
-        __syncthreads();
     }
 }
 
@@ -1950,7 +1967,7 @@ KernelTable make_table(bool read_pops)
     constexpr int D = Lat<LAT>::D;
     t.smem_sweep = SweepPlan<D, T, U>::BYTES;
     t.smem_force = size_t(ForcePlan<D>::R) * ForcePlan<D>::RP * sizeof(T);
-    t.smem_derivs = size_t(TL::NZR) * 6 * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
+    t.smem_derivs = size_t(DerivsPlan<D, T>::R) * 6 * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
     t.smem_collide = size_t(CollidePlan<D>::R) * (1 + AuxLayout<D>::NB + D) * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
     cudaFuncSetAttribute(t.force, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_force));
     cudaFuncSetAttribute(t.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_sweep));
