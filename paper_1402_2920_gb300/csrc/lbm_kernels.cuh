@@ -937,10 +937,10 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
 
 // ---------------------------------------------------------------------------
 // Tiled kernels.  A CTA owns TX x TY columns of one z-slab and marches along z
-// (2.5D blocking): each plane it loads is kept in a shared-memory ring of 5
-// planes (the reach of the Sec. IV.B first derivative is 2), so x and y
-// derivatives read the current plane and z derivatives the ring.  In 2D the
-// ring is the single plane.
+// (2.5D blocking): each plane it loads is kept in a shared-memory ring that
+// holds the 5 planes the Sec. IV.B first derivative reaches (2 on each side)
+// plus those in flight, so x and y derivatives read the current plane and z
+// derivatives the ring.  In 2D the ring is the single plane.
 // ---------------------------------------------------------------------------
 template <int D>
 struct Tile {
@@ -1540,7 +1540,8 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
     }
 }
 
-// Ring of the collision kernel: the 5 planes of the derivative stencil and PF planes in flight.
+// Ring of the collision kernel: the 5 planes of the derivative stencil and PF planes in flight;
+// the copy into the next slot starts after the plane's barrier (one barrier per plane).
 template <int D>
 struct CollidePlan {
     static constexpr int PF = D == 3 ? 1 : 0;
