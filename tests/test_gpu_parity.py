@@ -108,6 +108,24 @@ def test_fp64_cold_start_usolve():
     assert rel_linf(g.populations()[idx], o.pops()) < 1e-12
 
 
+# Several z-slabs of the tiled kernels (32 planes each, the last one ragged), so that every ring
+# slot is reused many times and CTAs meet at slab boundaries; nx = 24 takes the vector copies of
+# all tiled kernels, nx = 22 only those of the collision and force (pairs of sites).
+@pytest.mark.parametrize("dims", [(24, 18, 70), (22, 17, 67)])
+def test_parity_across_z_slabs(dims):
+    case = W.make_case("droplet3d", dims=dims)
+    g, o = _run_both(case, 3)
+    idx = perm_to_oracle(case.lattice)
+    assert rel_linf(g.populations()[idx], o.pops()) < 1e-12
+    g32 = lib_sim(case, storage=P.LBM_STORE_F32_DEV)
+    g32.init(case.rho, case.u)
+    g32.step(3)
+    rho_g, u_g = g32.fields()
+    rho_o, u_o, _ = o.fields()
+    assert rel_linf(rho_g, rho_o) < 1e-6
+    assert u_err(u_g, u_o, o.cs0) < 5e-4
+
+
 @pytest.mark.parametrize("name,dims,nsteps", [("slab2d", (61, 47), 50), ("droplet3d", (21, 18, 23), 10)])
 @pytest.mark.parametrize("storage,tol_rho,tol_u", [(P.LBM_STORE_F32_DEV, 1e-6, 5e-4), (P.LBM_STORE_F32, 5e-6, 2e-3),
                                                    (P.LBM_STORE_F32_LOC, 1e-6, 5e-4)])
