@@ -1041,16 +1041,17 @@ struct SweepPlan {
 };
 
 // S3-S6 fused: one sweep of the u-solve, iterated in u = (j0' + j~)/rho (the same iteration
-// as in j~, which the paper uses).  The CTA marches along z; per plane zl (two barriers):
+// as in j~, which the paper uses).  The CTA marches along z; per phase zl (one barrier):
 //   fetch    plane zl + PF of u and rho - rho0 (in-plane halo 4) into the ring, asynchronously;
-//   stage Q  q_ab of plane zq = zl - 2 (in-plane halo 2; the z derivatives read the ring)
-//            into one of two plane buffers;
-//   stage J  at the thread's own site: the in-plane part d_x q_ax + d_y q_ay of plane zq, and
-//            q_az(zq) scattered into the z-derivative sums of planes zq-2 .. zq+2, which live
-//            in registers.  Plane zq - 2 is then complete: j~new = -(1/12) d_b q_ab (S5),
+//   stage J  at the thread's own site, for the plane zs = zq - 1 that the previous phase's
+//            stage Q wrote: the in-plane part d_x q_ax + d_y q_ay of plane zs, and q_az(zs)
+//            scattered into the z-derivative sums of planes zs-2 .. zs+2, which live in
+//            registers.  Plane zs - 2 is then complete: j~new = -(1/12) d_b q_ab (S5),
 //            J(u) = (j0' + j~new)/rho, the update d = c1 d_prev + c2 (J(u) - u), u += d, and
-//            the S6 difference rho |d| = |j~new - j~| of the resulting j~ iterates.
-// In 2D the march is the single plane and the J stage finishes it directly.
+//            the S6 difference rho |d| = |j~new - j~| of the resulting j~ iterates;
+//   stage Q  q_ab of plane zq = zl - 2 (in-plane halo 2; the z derivatives read the ring)
+//            into the other of the two q plane buffers.
+// In 2D the march is the single plane: stage Q in the first phase, stage J in the second.
 template <int LAT, typename T, typename U>
 __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2 : 1) k_sweep(DevSim p, int pair)
 {
@@ -1155,26 +1156,98 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2
         cp_async_commit();
     }
     fetch_j(z0);
-    for (int zl = z0 - HZ; zl < z1 + HZ; ++zl) {
-        // the ring slot of plane zl + PF held plane zl + PF - R, last read before the
-        // second barrier of the previous step
-        if (zl + PF < z1 + HZ) fetch(zl + PF);
-        cp_async_commit();
-        cp_async_wait<PF>();  // plane zl has landed (this thread's copies)
-        __syncthreads();      // ... and everyone's
-        const int zj = zl - HZ;  // the plane that stage J finishes in this step
+    // q_ab of plane z lives in one of two plane buffers
+    auto qbuf = [&](int z) { return sq + (D == 3 ? (z & 1) : 0) * NQ * QP; };
+    auto qplane = [&](int z) { return D == 2 ? z == 0 : (z >= z0 - 2 && z < z1 + 2); };
+    // Phase zl (one barrier): stage J of plane zs = zq - 1, from the q that the previous phase
+    // wrote, and stage Q of plane zq = zl - HZ/2 into the other q buffer.  The J stage of plane zs
+    // finishes plane zs - 2 (3D), whose own u and rho - rho0 the previous phase read from the
+    // ring; the last phase only finishes.
+    for (int zl = z0 - HZ; zl < z1 + HZ + 1; ++zl) {
+        if (PF == 0) {  // 2D: the single plane, in the first phase
+            if (zl < z1 + HZ) fetch(zl);
+            cp_async_commit();
+        }
+        cp_async_wait<PF == 0 ? 0 : PF - 1>();  // plane zl has landed (this thread's copies)
+        __syncthreads();                         // ... and everyone's; the previous phase is done
+        // The ring slot of plane zl + PF held plane zl + PF - R = zl - 5, which only the previous
+        // phase read.
+        if (PF > 0) {
+            if (zl + PF < z1 + HZ) fetch(zl + PF);
+            cp_async_commit();
+        }
+        const int zq = zl - HZ / 2, zs = zq - 1;
+        if (qplane(zs)) {  // stage J: plane zs, whose q the previous phase wrote
+            const U* qb = qbuf(zs);
+            const int qi = (iy + 2) * UX + ix + 2;
+            if (zs >= z0 && zs < z1) {  // in-plane derivatives of plane zs
+                const U* ql[5];
+#pragma unroll
+                for (int k = 0; k < 5; ++k) ql[k] = qb;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    U acc = U(0);
+#pragma unroll
+                    for (int b = 0; b < 2; ++b) {
+                        const int c = sym2<D>(a, b);
+                        acc += d1p<U>(ql, b, qi, UX, [&](const U* P, int j) { return P[c * QP + j]; });
+                    }
+                    A[2][a] += acc;
+                }
+            }
+            if (D == 3) {
+                // d_z g(z) = (2/3)(g(z+1) - g(z-1)) - (1/12)(g(z+2) - g(z-2)): the share of
+                // g(zs) = q_az(zs) in the planes zs-2 .. zs+2
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const U v = qb[sym2<D>(a, 2) * QP + qi];
+                    A[0][a] -= U(1.0 / 12.0) * v;
+                    A[1][a] += U(2.0 / 3.0) * v;
+                    A[3][a] -= U(2.0 / 3.0) * v;
+                    A[4][a] += U(1.0 / 12.0) * v;
+                }
+            }
+            constexpr int KC = D == 3 ? 0 : 2;  // the finished plane: zs - 2 (3D), zs (2D)
+            const int zc = D == 3 ? zs - 2 : zs;
+            if (own && zc >= z0 && zc < z1) {
+                const long long g = (D == 3 ? zc * NP : 0) + own_xy;
+                const U rho = phys<U>(p).rho0 + jr;
+                const U irho = U(1) / rho;
+#pragma unroll
+                for (int a = 0; a < D; ++a) {
+                    const U jt_new = -(U(1) / U(12)) * A[KC][a];  // S5
+                    // residual of the fixed point u = (j0' + j~(u))/rho, the update d, u += d
+                    const U res = (pj[a] + jt_new) * irho - ju[a];
+                    U d = c2 * res;
+                    if (use_d) d += c1 * pd[a];
+                    if (keep_d) dvec[a * p.N + g] = d;
+                    unew[a * p.N + g] = ju[a] + d;
+                    const U dv = fabs(rho * d);  // |j~new - j~| of the j~ iterates
+                    bad |= !(dv == dv);
+                    dmax = fmax(dmax, dv);
+                    jmax = fmax(jmax, fabs(jt_new));
+                }
+            }
+            if (D == 3) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+#pragma unroll
+                    for (int a = 0; a < 3; ++a) A[k][a] = A[k + 1][a];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) A[4][a] = U(0);
+            }
+            fetch_j(zc + 1);
+        }
+        const int zj = zl - HZ;  // own u and rho - rho0 of the plane the next phase finishes
         if (zj >= z0 && zj < z1) {
-            // read before the second barrier: the next step's fetch may reuse this slot
             const U* uc = su + slot(zj) * D * UP;
             const int ui = (iy + 4) * UX + ix + 4;
 #pragma unroll
             for (int a = 0; a < D; ++a) ju[a] = uc[a * UP + ui];
             jr = U(sr[slot(zj) * UP + ui]);
         }
-        const int zq = zl - HZ / 2;
-        const bool qplane = D == 2 || (zq >= z0 - 2 && zq < z1 + 2);
-        U* qb = sq + (D == 3 ? (zq & 1) : 0) * NQ * QP;
-        if (qplane) {  // stage Q: plane zq, two x-neighbouring points per thread (64-bit reads)
+        if (qplane(zq)) {  // stage Q: plane zq, two x-neighbouring points per thread (64-bit reads)
+            U* qb = qbuf(zq);
             const U* pl[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) pl[k] = su + slot(D == 3 ? zq - 2 + k : 0) * D * UP;
@@ -1220,67 +1293,6 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2
 #pragma unroll
                 for (int c = 0; c < NQ; ++c) st2<U>(qb + c * QP + k, qv[0][c], qv[1][c]);
             }
-        }
-        __syncthreads();
-        if (qplane) {  // stage J
-            const int qi = (iy + 2) * UX + ix + 2;
-            if (zq >= z0 && zq < z1) {  // in-plane derivatives of plane zq
-                const U* ql[5];
-#pragma unroll
-                for (int k = 0; k < 5; ++k) ql[k] = qb;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    U acc = U(0);
-#pragma unroll
-                    for (int b = 0; b < 2; ++b) {
-                        const int c = sym2<D>(a, b);
-                        acc += d1p<U>(ql, b, qi, UX, [&](const U* P, int j) { return P[c * QP + j]; });
-                    }
-                    A[2][a] += acc;
-                }
-            }
-            if (D == 3) {
-                // d_z g(z) = (2/3)(g(z+1) - g(z-1)) - (1/12)(g(z+2) - g(z-2)): the share of
-                // g(zq) = q_az(zq) in the planes zq-2 .. zq+2
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const U v = qb[sym2<D>(a, 2) * QP + qi];
-                    A[0][a] -= U(1.0 / 12.0) * v;
-                    A[1][a] += U(2.0 / 3.0) * v;
-                    A[3][a] -= U(2.0 / 3.0) * v;
-                    A[4][a] += U(1.0 / 12.0) * v;
-                }
-            }
-            constexpr int KC = D == 3 ? 0 : 2;  // the finished plane: zq - 2 (3D), zq (2D)
-            const int zc = D == 3 ? zq - 2 : zq;
-            if (own && zc >= z0 && zc < z1) {
-                const long long g = (D == 3 ? zc * NP : 0) + own_xy;
-                const U rho = phys<U>(p).rho0 + jr;
-                const U irho = U(1) / rho;
-#pragma unroll
-                for (int a = 0; a < D; ++a) {
-                    const U jt_new = -(U(1) / U(12)) * A[KC][a];  // S5
-                    // residual of the fixed point u = (j0' + j~(u))/rho, the update d, u += d
-                    const U res = (pj[a] + jt_new) * irho - ju[a];
-                    U d = c2 * res;
-                    if (use_d) d += c1 * pd[a];
-                    if (keep_d) dvec[a * p.N + g] = d;
-                    unew[a * p.N + g] = ju[a] + d;
-                    const U dv = fabs(rho * d);  // |j~new - j~| of the j~ iterates
-                    bad |= !(dv == dv);
-                    dmax = fmax(dmax, dv);
-                    jmax = fmax(jmax, fabs(jt_new));
-                }
-            }
-            if (D == 3) {
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-#pragma unroll
-                    for (int a = 0; a < 3; ++a) A[k][a] = A[k + 1][a];
-#pragma unroll
-                for (int a = 0; a < 3; ++a) A[4][a] = U(0);
-            }
-            fetch_j(zc + 1);
         }
     }
     cp_async_wait<0>();
