@@ -41,6 +41,28 @@ def test_host_only_entry_points(lib):
     assert P.lbm_footprint_bytes(P.LBM_D3Q59, (256, 256, 3), P.LBM_STORE_F32) == 0  # invalid dims
 
 
+def test_size_limits(lib):
+    """lbm_create and lbm_footprint_bytes share one validation (host only): at most 2^31 - 1 sites
+    (32-bit site offsets in the streaming kernel), ny <= 524280 (the tiled kernels' grid rows),
+    at least 4 sites per axis, nz = 1 exactly in 2D."""
+    fp = P.lbm_footprint_bytes
+    ok = fp(P.LBM_D3Q59, (1024, 1024, 2047), P.LBM_STORE_F32_DEV)  # 2^31 - 2^20 sites
+    assert ok > 1024 * 1024 * 2047 * 2 * 58 * 4
+    assert fp(P.LBM_D3Q59, (1024, 1024, 2048), P.LBM_STORE_F32_DEV) == 0  # 2^31 sites
+    assert fp(P.LBM_D3Q59, (4, 524280, 4), P.LBM_STORE_F32_DEV) > 0
+    assert fp(P.LBM_D3Q59, (4, 524281, 4), P.LBM_STORE_F32_DEV) == 0
+    assert fp(P.LBM_D3Q59, (4, 4, 4), P.LBM_STORE_F16_LOC) > 0
+    assert fp(P.LBM_D3Q59, (4, 4, 3), P.LBM_STORE_F16_LOC) == 0
+    assert fp(P.LBM_D2Q21, (4, 4, 1), P.LBM_STORE_F32) > 0
+    assert fp(P.LBM_D2Q21, (4, 4, 2), P.LBM_STORE_F32) == 0
+    assert fp(P.LBM_D2Q21, (16, 16, 1), 8) == 0  # no such storage
+    assert fp(2, (16, 16, 16), P.LBM_STORE_F32) == 0  # no such lattice
+    # 16-bit storages need less memory per site than FP32, the local references a little more
+    n = (64, 64, 64)
+    assert fp(P.LBM_D3Q59, n, P.LBM_STORE_F16_DEV) < fp(P.LBM_D3Q59, n, P.LBM_STORE_F16_LOC) \
+        < fp(P.LBM_D3Q59, n, P.LBM_STORE_F32_DEV) < fp(P.LBM_D3Q59, n, P.LBM_STORE_F32_LOC)
+
+
 def test_no_cpu_fallback_without_gpu(lib):
     try:
         import torch
