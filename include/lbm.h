@@ -88,7 +88,9 @@ typedef struct {
                               and of the deviation storages                               */
     int storage;           /* LBM_STORE_*                                                 */
     int usolve_precision;  /* LBM_USOLVE_*                                                */
-    double usolve_tol;     /* stop when max|j~new - j~| <= usolve_tol + usolve_rtol max|j~new|;
+    double usolve_tol;     /* stop when max|j~new - j~| of the plain iteration (S6) and, with
+                              relaxation or Chebyshev acceleration, the largest update rho |du|
+                              the sweep applied are both <= usolve_tol + usolve_rtol max|j~new|;
                               both <= 0 select the default: 1e-14 for an FP64 u-solve; else
                               5e-9 (32-bit storages) or 4e-8 (16-bit storages), below the
                               rounding noise the stored populations put into j0 each step   */
@@ -247,8 +249,8 @@ const char* lbm_error_string(int code);
 
 /* Mass and momentum of a population array, computed without allocating anything.
  *   The sums are those lbm_stats_get reports, rho = sum_i n_i and j = sum_i n_i c_i
- *   over all sites (Sec. II).  The paper has no counterpart of the no-allocation form:
- *   it exists for callers that may not use the device allocator, such as a serving
+ *   over all sites.  The paper has no counterpart of this entry point: it exists for
+ *   callers that may not use the device allocator, such as a serving
  *   loop that has handed its whole memory budget to admitted simulations, or a monitor
  *   of running simulations that must not synchronise the device.
  *   lattice: LBM_D2Q21 or LBM_D3Q59.  pops: device pointer to FP64 populations
@@ -261,7 +263,9 @@ const char* lbm_error_string(int code);
  *   Caller memory is borrowed for the duration of the kernels.
  *   Scratch: one 128 KB device array per device, shared by all calls; its address is
  *   looked up (cudaGetSymbolAddress) on the first call made on each device, with that
- *   device current, so make that first call before any stream capture starts.  Nothing
+ *   device current, so make that first call before any stream capture starts.  The
+ *   address is kept for the life of the process: after cudaDeviceReset (or anything
+ *   else that replaces the device's primary context) do not call this again.  Nothing
  *   in the scratch must start at zero.  Calls on one device whose kernels may overlap
  *   (different streams, or host threads) race on the scratch; calls ordered on one
  *   stream do not.  Errors: LBM_E_INVALID_ARG (lattice, NULL pointer, n_sites out of

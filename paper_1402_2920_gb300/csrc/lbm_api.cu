@@ -656,7 +656,13 @@ int lbm_init(lbm_sim* s, const double* rho, const double* u, int on_device)
     const size_t N = size_t(s->dev.N);
     const double* drho = rho;
     const double* du = u;
-    double* tmp = nullptr;
+    // staging buffer of host inputs, released on every return path (stream-ordered)
+    struct Staging {
+        double* p = nullptr;
+        cudaStream_t st;
+        ~Staging() { if (p) (void)cudaFreeAsync(p, st); }
+    } stage{nullptr, s->stream};
+    double*& tmp = stage.p;
     if (!on_device) {
         LBM_CK(cudaMallocAsync(&tmp, (1 + s->d) * N * sizeof(double), s->stream));
         LBM_CK(cudaMemcpyAsync(tmp, rho, N * sizeof(double), cudaMemcpyHostToDevice, s->stream));
@@ -673,7 +679,11 @@ int lbm_init(lbm_sim* s, const double* rho, const double* u, int on_device)
     const int B = s->kt.block, G = nblocks(s->dev.N, B);
     if (s->kt.init_ref) LBM_CK(launch(s, s->kt.init_ref, G, B, s->dev, drho, 0));
     LBM_CK(launch(s, s->kt.init_eq, G, B, s->dev, drho, du, 0));
-    if (tmp) LBM_CK(cudaFreeAsync(tmp, s->stream));
+    if (tmp) {
+        double* p = tmp;
+        tmp = nullptr;
+        LBM_CK(cudaFreeAsync(p, s->stream));
+    }
     return LBM_OK;
 }
 

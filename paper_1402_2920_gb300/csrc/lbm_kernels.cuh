@@ -6,7 +6,9 @@
 //   k_moments   S1      rho = sum n_i, j0 = sum n_i c_i, c_s^2 window check
 //   k_force     S2      f = kappa rho d_a d_b d_b rho (Sec. IV.E), j0' = j0 + f/2
 //   k_sweep     S3-S6   one Jacobi sweep of the u-solve, tiled: u = (j0' + j~)/rho,
-//                       d_a u_b (Sec. IV.B), q_ab, j~new = -(1/12) d_b q_ab, max|j~new - j~|
+//                       d_a u_b (Sec. IV.B), q_ab, j~new = -(1/12) d_b q_ab; the stop test
+//                       takes max|j~new - j~| of the plain iteration (S6) and the size of the
+//                       accelerated update
 //   k_us_ctl    S6, S7  convergence test, buffer swap, graph loop condition
 //   k_derivs    S8-S11  u, j; first derivatives (tiled); A, B, C; the site-local
 //                       parts of Sigma and the whole Xi'
@@ -1222,7 +1224,11 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2
                     if (use_d) d += c1 * pd[a];
                     if (keep_d) dvec[a * p.N + g] = d;
                     unew[a * p.N + g] = ju[a] + d;
-                    const U dv = fabs(rho * d);  // |j~new - j~| of the j~ iterates
+                    // S6: |j~new - j~| of the plain iteration from the current iterate is rho |res|.
+                    // The accelerated update d can be small while res is not (its momentum term
+                    // c1 d_prev cancelling c2 res), and large while res is small (the momentum term
+                    // still moving the iterate), so the stop needs both below the tolerance.
+                    const U dv = rho * fmax(fabs(res), fabs(d));
                     bad |= !(dv == dv);
                     dmax = fmax(dmax, dv);
                     jmax = fmax(jmax, fabs(jt_new));
