@@ -252,11 +252,11 @@ def run_native(args):
     a, b, T = case.eos_abT
     stream = torch.cuda.current_stream()
 
-    def make_sim(st):
+    def make_sim(st, usolve=P.LBM_USOLVE_NATIVE):
         # u-solve sweeps Chebyshev-accelerated for the spectrum bound g over the workload's density range
         prm = P.make_params(gamma=case.gamma, kappa=case.kappa, rho0=case.rho0, storage=st,
                             rho_check_min=0.98 * case.eos.rho_g, rho_check_max=1.02 * case.eos.rho_l,
-                            usolve_omega=0.0, usolve_chebyshev=1)
+                            usolve_omega=0.0, usolve_chebyshev=1, usolve_precision=usolve)
         return P.Sim(case.lattice, case.dims, P.make_eos(P.LBM_EOS_VDW, a=a, b=b, T=T), prm, stream.cuda_stream)
 
     def timed(sim, K, Wm):
@@ -313,17 +313,35 @@ def run_native(args):
     # the FP16-deviation storage form of the same workload
     # the 16-bit storage forms of the same workload: deviations from w_i(rho0) rho0, and from the
     # sender's local w_i(rho) rho (error against FP64: see the configuration tests)
+    # and the FP32 storage with the u-solve's sweeps in FP64 (the fixed point to FP64 tolerance)
     extra = {}
     if args.storage in ("f32", "f32dev") and not args.no_extras:
         del sim
         torch.cuda.empty_cache()
-        for key, st in (("fp16_dev_storage", "f16dev"), ("fp16_local_storage", "f16loc")):
-            sim16 = make_sim(STORAGES[st])
-            ms16, _, sweeps16, _ = timed(sim16, K, Wm)
-            extra[key] = {"value": whole_job_mlups(ws, N, K, ms16 / 1e3), "unit": UNIT, "speedup_vs_f32": ms / ms16,
-                          "ms_per_step": ms16 / K, "usolve_sweeps_per_step": sweeps16 / K}
-            del sim16
+        legs = (("fp16_dev_storage", "f16dev", P.LBM_USOLVE_NATIVE), ("fp16_local_storage", "f16loc", P.LBM_USOLVE_NATIVE),
+                ("bf16_dev_storage", "bf16dev", P.LBM_USOLVE_NATIVE), ("bf16_local_storage", "bf16loc", P.LBM_USOLVE_NATIVE),
+                ("fp64_usolve", args.storage, P.LBM_USOLVE_F64))
+        for key, st, us in legs:
+            simx = make_sim(STORAGES[st], us)
+            msx, _, sweepsx, _ = timed(simx, K, Wm)
+            extra[key] = {"value": whole_job_mlups(ws, N, K, msx / 1e3), "unit": UNIT, "speedup_vs_f32": ms / msx,
+                          "ms_per_step": msx / K, "usolve_sweeps_per_step": sweepsx / K,
+                          "storage": st, "usolve": "FP64 sweeps, |dj~| <= 1e-14" if us == P.LBM_USOLVE_F64 else
+                          "native-precision sweeps"}
+            del simx
             torch.cuda.empty_cache()
+        # the sweep's tensor-copy (TMA) form against its per-thread-copy form (the default)
+        os.environ["LBM_SWEEP_COPY"] = "tma"
+        try:
+            simx = make_sim(storage)
+            msx, _, _, _ = timed(simx, K, Wm)
+            profx = P.lbm_profile(simx.handle, reps=5)
+        finally:
+            del os.environ["LBM_SWEEP_COPY"]
+        extra["sweep_tma"] = {"usolve_sweep_ms": profx["usolve_sweep"], "usolve_sweep_ms_cp_async": prof["usolve_sweep"],
+                              "ms_per_step": msx / K, "value": whole_job_mlups(ws, N, K, msx / 1e3), "unit": UNIT}
+        del simx
+        torch.cuda.empty_cache()
         sim = make_sim(storage)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
@@ -353,9 +371,9 @@ def run_native(args):
         from paper_1402_2920_gb300 import serving as S
 
         st, _, _ = S.run(n=args.serving_requests, load=0.8, calibrate=min(24, args.serving_requests))
-        serving = dict(st, unit="s", workload="first %d requests of the seed-1 stream (droplets, D2Q21 64^2-512^2 "
+        serving = dict(st, unit="s", workload="%s %d requests of the seed-1 stream (droplets, D2Q21 64^2-512^2 "
                                                "and D3Q59 32^3-128^3, 500-5000 steps, FP32 deviations)"
-                       % args.serving_requests)
+                       % ("all" if args.serving_requests >= 256 else "first", args.serving_requests))
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_extras:
@@ -399,7 +417,7 @@ def main():
     # the benchmark workload is the 256^3 cube; smaller cubes of the same recipe serve profiling
     ap.add_argument("--side", type=int, default=256)
     # requests of the serving stream to replay (256 is the whole stream; 0 skips it)
-    ap.add_argument("--serving-requests", type=int, default=32)
+    ap.add_argument("--serving-requests", type=int, default=256)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

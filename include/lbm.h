@@ -66,7 +66,7 @@ enum {
     LBM_E_USOLVE_DIVERGED = -4, /* u-solve hit its sweep cap or produced non-finite j~   */
     LBM_E_OOM = -5,             /* device allocation failed                              */
     LBM_E_CUDA = -6,            /* a CUDA call failed or no device is usable             */
-    LBM_E_TIMEOUT = -7,         /* reserved: a bounded device wait ran out               */
+    LBM_E_TIMEOUT = -7,         /* a bounded device wait (on a tensor copy) ran out      */
     LBM_E_IO = -8               /* lbm_save / lbm_load file error or mismatched header   */
 };
 
@@ -226,17 +226,24 @@ typedef struct {
 
 typedef struct {
     size_t memory_budget;   /* device bytes for simulations; 0: 90 % of free memory     */
-    int max_active;         /* simulations resident at once (one stream each)           */
+    int max_active;         /* simulations resident at once                             */
     int chunk_steps;        /* steps issued to a simulation per turn of the loop        */
+    int batched;            /* 1: the resident simulations of each kernel combination (lattice,
+                               storage, u-solve precision, gamma = 0 or not) step together, one
+                               persistent launch per stage over all of them, at most 32 per
+                               combination; 0: one stream and one graph launch per simulation */
 } lbm_serve_config;
 
 /* Run a stream of requests to completion on the current device (continuous batching).
  *   A request is admitted once it has arrived, a slot is free and its footprint
  *   (lbm_footprint_bytes) fits in the budget beside the running ones, in arrival order.
- *   Admitted simulations stay resident and advance chunk_steps at a time on their own
- *   streams, so their work overlaps on the device; finished ones hand their fields to
- *   rho_out / u_out, free their slot and memory, and the next arrivals take them.  Each
- *   result equals that of the same simulation stepped alone.  Blocks until every
+ *   Admitted simulations stay resident and advance chunk_steps at a time: with batched = 1
+ *   in batched launches per kernel combination (a combination's batch takes its next chunk
+ *   once the previous one has finished, admitting waiting requests in between; the
+ *   combinations run on streams of their own), with batched = 0 each on its own stream.
+ *   Finished ones hand their fields to rho_out / u_out, free their slot and memory, and
+ *   the next arrivals take them.  Each result equals that of the same simulation stepped
+ *   alone.  Blocks until every
  *   request is done; per-request times and statuses go to out[n].  A request that can
  *   never fit gets LBM_E_OOM, an invalid one LBM_E_INVALID_ARG; neither stops the
  *   others.  Returns LBM_E_INVALID_ARG for bad arguments, LBM_E_CUDA when streams or

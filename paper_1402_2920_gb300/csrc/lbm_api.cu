@@ -15,7 +15,10 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "lbm.h"
+#include "lbm_batch.h"
 #include "lbm_common.h"
 #include "lbm_lattice.h"
 
@@ -40,6 +43,7 @@ struct lbm_sim {
     lbm_eos eos{};
     lbm_params prm{};
     KernelTable kt{};
+    const void* sweep = nullptr;  // the sweep kernel in use: kt.sweep, or kt.sweep_tma when selected
     DevSim dev{};
     int cur = 0;  // population buffer holding the current pre-collision populations
     int64_t steps = 0;
@@ -47,6 +51,7 @@ struct lbm_sim {
     double* red_part = nullptr;
     double* red_out = nullptr;
     Graphs one[2], two[2];
+    bool graphs = false;  // the step graphs are built on the first lbm_step
 };
 
 namespace {
@@ -146,6 +151,13 @@ void fill_phys(Phys<T>& q, const DevSim& dv, const lbm_eos& e)
     q.Teos = T(e.T);
     q.bT = T(e.b * e.T);
     q.g0 = T(1.0 - e.b * dv.rho0);
+    {
+        const double g0 = 1.0 - e.b * dv.rho0;
+        const double F0 = e.b * e.T / (g0 * g0) - e.a;
+        q.F0 = T(F0);
+        q.F0lo = T(F0 - double(T(F0)));
+        q.b2T_g02 = T(e.b * e.b * e.T / (g0 * g0));
+    }
     const double D = e.kind == LBM_EOS_PSI_SINE ? e.rho2 - e.rho1 : 1.0;
     q.rho1 = T(e.rho1);
     q.rho3 = T(2.0 * e.rho2 - e.rho1);
@@ -264,7 +276,7 @@ int add_step(lbm_sim* s, cudaGraph_t g, cudaGraphNode_t dep, int src, cudaGraphN
     {
         cudaGraphNode_t b1, b3;
         void* a1[] = {&dv, &pair};
-        LBM_CK(add_kernel(body, &b1, s->kt.sweep, TG, TB, a1, nullptr, 0, s->kt.smem_sweep));
+        LBM_CK(add_kernel(body, &b1, s->sweep, TG, TB, a1, nullptr, 0, s->kt.smem_sweep));
         void* a3[] = {&dv, &pair, &h, &one};
         LBM_CK(add_kernel(body, &b3, s->kt.us_ctl, dim3(1), 1, a3, &b1, 1));
     }
@@ -344,9 +356,74 @@ int read_status(lbm_sim* s, int* bits)
 
 int status_code(int bits)
 {
+    if (bits & STB_TIMEOUT) return LBM_E_TIMEOUT;
     if (bits & (STB_WEIGHTS | STB_NONFINITE_RHO)) return LBM_E_WEIGHTS;
     if (bits & (STB_USOLVE_CAP | STB_USOLVE_NAN)) return LBM_E_USOLVE_DIVERGED;
     return LBM_OK;
+}
+
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+using EncodeTiledFn = PFN_cuTensorMapEncodeTiled_v12000;
+EncodeTiledFn tensor_map_encoder()
+{
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            (void)cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Tensor map of a field [ncomp][nz][ny][nx] (rank 3 when ncomp = 1) read in boxes of one plane of
+// box_x x box_y sites, out-of-range elements read as zero.
+bool encode_plane_map(CUtensorMap* m, void* base, int ncomp, size_t esize, const DevSim& dv, const int box[2])
+{
+    const EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc || !base) return false;
+    const cuuint32_t rank = ncomp > 1 ? 4 : 3;
+    const cuuint64_t dims[4] = {cuuint64_t(dv.nx), cuuint64_t(dv.ny), cuuint64_t(dv.nz), cuuint64_t(ncomp)};
+    const cuuint64_t strides[3] = {cuuint64_t(dv.nx) * esize, cuuint64_t(dv.nx) * cuuint64_t(dv.ny) * esize,
+                                   cuuint64_t(dv.N) * esize};
+    const cuuint32_t boxd[4] = {cuuint32_t(box[0]), cuuint32_t(box[1]), 1, 1};
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    const CUresult r = enc(m, esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, rank, base,
+                           dims, strides, boxd, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// The sweep kernel: per-thread plane copies, or with LBM_SWEEP_COPY=tma in the environment the
+// tensor-copy form, whose tensor maps need a 3D lattice with rows a multiple of 16 bytes.  The
+// per-thread form is the default: it is the faster of the two (the sweep is bound by its
+// shared-memory reads and instruction issue, not by issuing the copies).
+void setup_sweep_maps(lbm_sim* s)
+{
+    DevSim& dv = s->dev;
+    dv.tma = 0;
+    dv.tmaps = nullptr;
+    s->sweep = s->kt.sweep;
+    const char* sel = std::getenv("LBM_SWEEP_COPY");
+    if (!sel || std::strcmp(sel, "tma") != 0 || !s->kt.sweep_tma) return;
+    if (s->d != 3 || !dv.aligned16 || dv.nx % 4 != 0) return;
+    SweepMaps m;
+    bool ok = true;
+    for (int pr = 0; pr < 2; ++pr)
+        for (int b = 0; b < 2; ++b)
+            ok = ok && encode_plane_map(&m.u[pr][b], dv.uit[pr][b], 3, s->kt.usize, dv, s->kt.sweep_box);
+    ok = ok && encode_plane_map(&m.rho, dv.rho, 1, s->kt.tsize, dv, s->kt.sweep_box);
+    void* dm = nullptr;
+    ok = ok && dev_alloc(s, &dm, sizeof(SweepMaps)) == LBM_OK;
+    ok = ok && cudaMemcpyAsync(dm, &m, sizeof(SweepMaps), cudaMemcpyHostToDevice, s->stream) == cudaSuccess &&
+         cudaStreamSynchronize(s->stream) == cudaSuccess;  // m lives on this stack
+    if (!ok) (void)cudaGetLastError();
+    dv.tmaps = ok ? static_cast<const SweepMaps*>(dm) : nullptr;
+    dv.tma = ok ? 1 : 0;
+    if (ok) s->sweep = s->kt.sweep_tma;
 }
 
 int reset_usolve(lbm_sim* s)
@@ -402,7 +479,7 @@ int run_fields(lbm_sim* s)
     cudaGraphConditionalHandle h{};
     const int no = 0;
     for (int it = 0; it < s->dev.maxit + 1; ++it) {
-        LBM_CK(launch_tiled(s, s->kt.sweep, s->kt.smem_sweep, dv, pair));
+        LBM_CK(launch_tiled(s, s->sweep, s->kt.smem_sweep, dv, pair));
         LBM_CK(launch(s, s->kt.us_ctl, 1, 1, dv, pair, h, no));
         UsolveState u;
         LBM_CK(cudaMemcpyAsync(&u, &dv.us[1], sizeof(u), cudaMemcpyDeviceToHost, s->stream));
@@ -631,6 +708,7 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
             for (int b = 0; b < 2; ++b) ok = ok && a16(dv.uit[pr][b]);
         dv.aligned16 = ok ? 1 : 0;
     }
+    setup_sweep_maps(s);
     // well-defined contents before the first lbm_init
     for (int b = 0; b < 2; ++b) {
         const size_t wbytes = dv.wref[b] ? size_t(lattice == LBM_D3Q59 ? 8 : 6) * N * sizeof(float) : 0;
@@ -642,7 +720,6 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
         }
     }
     rc = reset_usolve(s);
-    if (!rc) rc = build_graphs(s);
     if (!rc && cudaStreamSynchronize(s->stream) != cudaSuccess) rc = LBM_E_CUDA;
     if (rc) { lbm_destroy(s); return rc; }
     *out = s;
@@ -709,7 +786,7 @@ int step_direct(lbm_sim* s)
     LBM_CK(launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair));
     LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
     for (int it = 0; it < dv.maxit + 1; ++it) {
-        LBM_CK(launch_tiled(s, s->kt.sweep, s->kt.smem_sweep, dv, pair));
+        LBM_CK(launch_tiled(s, s->sweep, s->kt.smem_sweep, dv, pair));
         LBM_CK(launch(s, s->kt.us_ctl, 1, 1, dv, pair, h, no));
         UsolveState u;
         LBM_CK(cudaMemcpyAsync(&u, &dv.us[0], sizeof(u), cudaMemcpyDeviceToHost, s->stream));
@@ -746,6 +823,11 @@ int lbm_step(lbm_sim* s, int64_t nsteps)
             s->steps += 1;
         }
         return LBM_OK;
+    }
+    if (!s->graphs && nsteps > 0) {  // built on first use: simulations stepped in batches never need them
+        const int rc = build_graphs(s);
+        if (rc) return rc;
+        s->graphs = true;
     }
     int64_t n = nsteps;
     while (n >= 2) {
@@ -901,7 +983,7 @@ int lbm_profile(lbm_sim* s, int reps, double* ms_out, int n)
             switch (k) {
             case 0: e = launch_moments(s, dv, src, pair); break;
             case 1: e = launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair); break;
-            case 2: e = launch_tiled(s, s->kt.sweep, s->kt.smem_sweep, dv, pair); break;
+            case 2: e = launch_tiled(s, s->sweep, s->kt.smem_sweep, dv, pair); break;
             case 3: e = launch_tiled(s, s->kt.derivs, s->kt.smem_derivs, dv); break;
             case 4: e = launch_tiled(s, s->kt.collide, s->kt.smem_collide, dv, src); break;
             }
@@ -1026,3 +1108,229 @@ int lbm_step_batch(lbm_sim* const* sims, int n, const int64_t* nsteps)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched stepping (lbm_batch.h)
+// ---------------------------------------------------------------------------
+namespace lbm {
+
+struct Batch {
+    KernelTable kt{};
+    int key = 0;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    DevSim* d_sims = nullptr;    // [kBatchSlots] device table
+    BatchWork* d_work = nullptr;
+    DevSim* h_sims = nullptr;    // pinned mirrors of the table and the work list (copied from
+    BatchWork* h_work = nullptr; // these asynchronously, so they change only between chunks)
+    cudaEvent_t copied = nullptr; // the mirrors' last copy to the device has been done
+    lbm_sim* slot[kBatchSlots] = {};
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t x = nullptr;
+};
+
+int batch_key(int lattice, const lbm_params& prm)
+{
+    const bool us64 = prm.storage == LBM_STORE_F64 || prm.usolve_precision == LBM_USOLVE_F64;
+    return ((lattice * 16 + prm.storage) * 2 + (us64 ? 1 : 0)) * 2 + (prm.gamma != 0.0 ? 1 : 0);
+}
+
+int batch_key_of(const lbm_sim* s) { return batch_key(s->lattice, s->prm); }
+
+namespace {
+
+// persistent grid of a batched kernel: the blocks that fit on the device at once
+int resident_grid(const void* fn, int threads, size_t smem)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, threads, smem) != cudaSuccess || per < 1) {
+        (void)cudaGetLastError();
+        per = 1;
+    }
+    return sms * per;
+}
+
+int build_batch_graph(Batch* b, int lattice)
+{
+    LBM_CK(cudaGraphCreate(&b->g, 0));
+    const KernelTable& kt = b->kt;
+    DevSim* sims = b->d_sims;
+    BatchWork* w = b->d_work;
+    int pair = 0;
+    const int TB = kt.tile_threads;
+    const int MB = kt.local_ref ? kMomentsRowBlock : kt.block;
+    cudaGraphNode_t n0, n1, n2, n3, nc, n5, n6, n7;
+    {
+        void* a[] = {&sims, &w};
+        LBM_CK(add_kernel(b->g, &n0, kt.kb_step_begin, dim3(1), 32, a, nullptr, 0));
+    }
+    {
+        void* a[] = {&sims, &w, &pair};
+        LBM_CK(add_kernel(b->g, &n1, kt.kb_moments, dim3(resident_grid(kt.kb_moments, MB, 0)), MB, a, &n0, 1));
+    }
+    {
+        void* a[] = {&sims, &w, &pair};
+        LBM_CK(add_kernel(b->g, &n2, kt.kb_force, dim3(resident_grid(kt.kb_force, TB, kt.smem_force)), TB, a, &n1, 1,
+                          kt.smem_force));
+    }
+    {
+        void* a[] = {&sims, &w, &pair};
+        LBM_CK(add_kernel(b->g, &n3, kt.kb_us_begin, dim3(1), 32, a, &n2, 1));
+    }
+    cudaGraphConditionalHandle h;
+    LBM_CK(cudaGraphConditionalHandleCreate(&h, b->g, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = h;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    LBM_CK(cudaGraphAddNode(&nc, b->g, &n3, nullptr, 1, &cp));
+    {
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        cudaGraphNode_t b1, b2;
+        void* a1[] = {&sims, &w, &pair};
+        LBM_CK(add_kernel(body, &b1, kt.kb_sweep, dim3(resident_grid(kt.kb_sweep, TB, kt.smem_sweep)), TB, a1, nullptr, 0,
+                          kt.smem_sweep));
+        void* a2[] = {&sims, &w, &pair, &h};
+        LBM_CK(add_kernel(body, &b2, kt.kb_us_ctl, dim3(1), 32, a2, &b1, 1));
+    }
+    {
+        void* a[] = {&sims, &w};
+        LBM_CK(add_kernel(b->g, &n5, kt.kb_derivs, dim3(resident_grid(kt.kb_derivs, TB, kt.smem_derivs)), TB, a, &nc, 1,
+                          kt.smem_derivs));
+    }
+    {
+        void* a[] = {&sims, &w};
+        LBM_CK(add_kernel(b->g, &n6, kt.kb_collide, dim3(resident_grid(kt.kb_collide, TB, kt.smem_collide)), TB, a, &n5,
+                          1, kt.smem_collide));
+    }
+    {
+        void* a[] = {&sims, &w};
+        LBM_CK(add_kernel(b->g, &n7, kt.kb_step_end, dim3(1), 32, a, &n6, 1));
+    }
+    (void)lattice;
+    LBM_CK(cudaGraphInstantiate(&b->x, b->g, 0));
+    return LBM_OK;
+}
+
+}  // namespace
+
+int batch_create(const lbm_sim* proto, cudaStream_t stream, Batch** out)
+{
+    if (!proto || !out) return LBM_E_INVALID_ARG;
+    *out = nullptr;
+    Batch* b = new (std::nothrow) Batch();
+    if (!b) return LBM_E_OOM;
+    b->kt = proto->kt;
+    b->key = batch_key_of(proto);
+    b->device = proto->device;
+    b->stream = stream;
+    int rc = LBM_OK;
+    if (cudaSetDevice(b->device) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&b->d_sims), sizeof(DevSim) * kBatchSlots) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&b->d_work), sizeof(BatchWork)) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&b->h_sims), sizeof(DevSim) * kBatchSlots) != cudaSuccess ||
+        cudaMallocHost(reinterpret_cast<void**>(&b->h_work), sizeof(BatchWork)) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->copied, cudaEventDisableTiming) != cudaSuccess) {
+        (void)cudaGetLastError();
+        rc = LBM_E_OOM;
+    }
+    if (!rc) {
+        std::memset(static_cast<void*>(b->h_sims), 0, sizeof(DevSim) * kBatchSlots);
+        std::memset(static_cast<void*>(b->h_work), 0, sizeof(BatchWork));
+        rc = build_batch_graph(b, proto->lattice);
+    }
+    if (rc) {
+        batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return LBM_OK;
+}
+
+int batch_attach(Batch* b, int slot, lbm_sim* s)
+{
+    if (!b || !s || slot < 0 || slot >= kBatchSlots || b->slot[slot] || batch_key_of(s) != b->key) return LBM_E_INVALID_ARG;
+    b->slot[slot] = s;
+    return LBM_OK;
+}
+
+void batch_detach(Batch* b, int slot)
+{
+    if (b && slot >= 0 && slot < kBatchSlots) b->slot[slot] = nullptr;
+}
+
+int batch_launch(Batch* b, const int64_t* steps)
+{
+    if (!b || !steps) return LBM_E_INVALID_ARG;
+    LBM_CK(cudaSetDevice(b->device));
+    LBM_CK(cudaEventSynchronize(b->copied));  // the mirrors may be rewritten
+    BatchWork& w = *b->h_work;
+    int nslot = 0;
+    int64_t most = 0;
+    for (int k = 0; k < kBatchSlots; ++k)
+        if (b->slot[k]) nslot = k + 1;
+    w.nslot = nslot;
+    w.tstart[0] = 0;
+    w.mstart[0] = 0;
+    for (int k = 0; k < kBatchSlots; ++k) {
+        lbm_sim* s = b->slot[k];
+        const int64_t n = s ? steps[k] : 0;
+        if (n < 0) return LBM_E_INVALID_ARG;
+        most = n > most ? n : most;
+        w.live[k] = 0;
+        w.todo[k] = int(n);
+        w.src[k] = s ? s->cur : 0;
+        int tiles = 0, mblocks = 0;
+        w.tgx[k] = w.tgy[k] = w.mgx[k] = w.mgy[k] = 1;
+        if (s) {
+            b->h_sims[k] = s->dev;
+            const dim3 tg = tile_grid(s), mg = moments_grid(s);
+            w.tgx[k] = int(tg.x);
+            w.tgy[k] = int(tg.y);
+            w.mgx[k] = int(mg.x);
+            w.mgy[k] = int(mg.y);
+            tiles = int(tg.x * tg.y * tg.z);
+            mblocks = int(mg.x * mg.y * mg.z);
+        }
+        w.tstart[k + 1] = w.tstart[k] + (k < nslot ? tiles : 0);
+        w.mstart[k + 1] = w.mstart[k] + (k < nslot ? mblocks : 0);
+    }
+    if (most == 0) return LBM_OK;
+    LBM_CK(cudaMemcpyAsync(b->d_sims, b->h_sims, sizeof(DevSim) * size_t(nslot), cudaMemcpyHostToDevice, b->stream));
+    LBM_CK(cudaMemcpyAsync(b->d_work, b->h_work, sizeof(BatchWork), cudaMemcpyHostToDevice, b->stream));
+    LBM_CK(cudaEventRecord(b->copied, b->stream));
+    for (int64_t i = 0; i < most; ++i) LBM_CK(cudaGraphLaunch(b->x, b->stream));
+    return LBM_OK;
+}
+
+void batch_account(Batch* b, const int64_t* steps)
+{
+    if (!b || !steps) return;
+    for (int k = 0; k < kBatchSlots; ++k) {
+        lbm_sim* s = b->slot[k];
+        if (!s || steps[k] <= 0) continue;
+        s->cur ^= int(steps[k] & 1);
+        s->steps += steps[k];
+    }
+}
+
+void batch_destroy(Batch* b)
+{
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->stream) cudaStreamSynchronize(b->stream);
+    if (b->x) cudaGraphExecDestroy(b->x);
+    if (b->g) cudaGraphDestroy(b->g);
+    if (b->d_sims) cudaFree(b->d_sims);
+    if (b->d_work) cudaFree(b->d_work);
+    if (b->h_sims) cudaFreeHost(b->h_sims);
+    if (b->h_work) cudaFreeHost(b->h_work);
+    if (b->copied) cudaEventDestroy(b->copied);
+    (void)cudaGetLastError();
+    delete b;
+}
+
+}  // namespace lbm

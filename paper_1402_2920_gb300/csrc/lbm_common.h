@@ -6,6 +6,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace lbm {
@@ -49,7 +50,7 @@ constexpr int kRedBlock = 256;
 constexpr int kRedGrid = 1024;
 
 // Error bits recorded by kernels (read back by lbm_sync and friends).
-enum StatusBits { STB_WEIGHTS = 1, STB_NONFINITE_RHO = 2, STB_USOLVE_CAP = 4, STB_USOLVE_NAN = 8 };
+enum StatusBits { STB_WEIGHTS = 1, STB_NONFINITE_RHO = 2, STB_USOLVE_CAP = 4, STB_USOLVE_NAN = 8, STB_TIMEOUT = 16 };
 
 // Physical parameters and derived constants in the kernel arithmetic T, filled on the
 // host so that device code neither converts from double nor divides per site.
@@ -57,6 +58,8 @@ template <typename T>
 struct Phys {
     T rho0, cs0, gamma, kappa, omega;
     T a, b, Teos, bT, g0;                 // van der Waals; bT = b T, g0 = 1 - b rho0
+    T F0, F0lo, b2T_g02;                  // slope of c_s^2 = p/rho at rho0, b T / g0^2 - a, as a pair
+                                          // F0 + F0lo; and b^2 T / g0^2 (c_s^2 differences)
     T rho1, rho3, cs2_1, A, pi_D, A_pi_D, AD_pi, ph0;  // psi-sine: pi/D, A pi/D, A D/pi, phase at rho0
     T cs2_lo, cs2_hi;                     // positive-weight window
     T w0[8], off[8];                      // w_k(c_s^2(rho0)) and w_k rho0 per shell
@@ -107,6 +110,32 @@ struct DevSim {
     int maxit, warm;
     Phys<float> pf;                  // the same parameters for FP32 arithmetic
     Phys<double> pd;                 // and for FP64 arithmetic
+    // Tensor maps of the sweep's plane loads (TMA) in device memory, valid when tma = 1.
+    const struct SweepMaps* tmaps;
+    int tma;
+};
+
+// The sweep's tensor maps: the u iterates uit[pair][buffer] as {nx, ny, nz, 3} and rho - rho0
+// as {nx, ny, nz}, each loaded in boxes of 40 x 16 sites (the tile with its in-plane halo of 4)
+// of one plane.
+struct SweepMaps {
+    CUtensorMap u[2][2];
+    CUtensorMap rho;
+};
+
+// Batched launches: up to kBatchSlots simulations of one kernel combination take their time
+// steps together, each stage one persistent launch whose blocks walk the work list of all of
+// them (a tile or block of one simulation per pass).  The table lives in device memory.
+constexpr int kBatchSlots = 32;
+struct BatchWork {
+    int nslot;                       // slots in use (0 .. kBatchSlots)
+    int live[kBatchSlots];           // 1: the slot takes the current step
+    int src[kBatchSlots];            // its current population buffer
+    int todo[kBatchSlots];           // steps it still takes in the running chunk
+    int tstart[kBatchSlots + 1];     // prefix sums of the tiled kernels' tile counts
+    int mstart[kBatchSlots + 1];     // prefix sums of the moments kernel's block counts
+    int tgx[kBatchSlots], tgy[kBatchSlots];  // tile grid extents in x and y
+    int mgx[kBatchSlots], mgy[kBatchSlots];  // moments grid extents in x and y
 };
 
 // Kernels of one (lattice, arithmetic, storage, u-solve arithmetic) combination.
@@ -114,7 +143,8 @@ struct KernelTable {
     const void* moments;      // (DevSim, int src, int pair)
     const void* force;        // (DevSim, int pair): also the u-solve's starting u
     const void* us_begin;     // (DevSim, int pair)
-    const void* sweep;        // (DevSim, int pair): one tiled u-solve sweep
+    const void* sweep;        // (DevSim, int pair): one tiled u-solve sweep, planes copied per thread
+    const void* sweep_tma;    // the same with tensor-copy (TMA) plane loads (3D; nullptr in 2D)
     const void* us_ctl;       // (DevSim, int pair, cudaGraphConditionalHandle, int use_cond)
     const void* derivs;       // (DevSim)
     const void* collide;      // (DevSim, int src)
@@ -126,12 +156,23 @@ struct KernelTable {
     const void* pops_in;      // (DevSim, const double* in, int dst)
     const void* red_partial;  // (DevSim, int src, double* partials)
     const void* red_final;    // (DevSim, const double* partials, int nparts, double* out)
+    // batched forms (const DevSim* sims, BatchWork* work, ...): see BatchWork
+    const void* kb_step_begin;  // (sims, work)
+    const void* kb_moments;     // (sims, work, int pair)
+    const void* kb_force;       // (sims, work, int pair)
+    const void* kb_us_begin;    // (sims, work, int pair)
+    const void* kb_sweep;       // (sims, work, int pair)
+    const void* kb_us_ctl;      // (sims, work, int pair, cudaGraphConditionalHandle)
+    const void* kb_derivs;      // (sims, work)
+    const void* kb_collide;     // (sims, work)
+    const void* kb_step_end;    // (sims, work)
     int block;                // threads per block of the per-site kernels
     int tile[3];              // TX, TY, ZB of the tiled kernels
     int tile_threads;
     size_t smem_force, smem_sweep, smem_derivs, smem_collide;  // dynamic shared memory bytes
     size_t tsize, usize, ssize;  // bytes of T, U and the storage type
     size_t rsize;                // bytes of a rest-plane element (0: no separate plane)
+    int sweep_box[2];            // in-plane box of the sweep's plane loads (tile plus halo 4)
     bool exact;                  // float-pair density bookkeeping (rho_lo is used)
     bool local_ref;              // the storage is relative to the sender's w_k rho (DevSim::wref)
 };

@@ -16,6 +16,8 @@
 //                       push streaming n_i(r + c_i) = n_i + Delta_i
 #pragma once
 
+#include <climits>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -194,10 +196,15 @@ __device__ __forceinline__ void cs2_delta(const DevSim& p, T drho, T& s, T& ds)
     const Phys<T>& q = phys<T>(p);
     const T rho = q.rho0 + drho;
     if (p.eos_kind == 0) {
-        // s = T/(1 - b rho) - a rho  =>  s - s0 = drho (T b / ((1 - b rho)(1 - b rho0)) - a)
-        const T g = T(1) - q.b * rho;
-        s = q.Teos / g - q.a * rho;
-        ds = drho * (q.bT / (g * q.g0) - q.a);
+        // s = T/(1 - b rho) - a rho  =>  s - s0 = drho F(rho), F(rho) = b T / ((1 - b rho)(1 - b rho0)) - a
+        // = F(rho0) + b^2 T drho / ((1 - b rho) (1 - b rho0)^2).  F(rho0) is a difference of O(1)
+        // terms; it comes precomputed as an unevaluated pair F0 + F0lo, so that ds carries one
+        // rounding of its own size instead of the cancellation of the O(1) terms (in FP32 that
+        // cancellation biased the lattice pressure of the bulk phases at ~1e-7).
+        const T g = q.g0 - q.b * drho;
+        const T corr = q.b2T_g02 * drho / g;
+        ds = fma(drho, q.F0, fma(drho, q.F0lo, drho * corr));
+        s = q.cs0 + ds;
     } else {
         // s = cs2(rho1) exp(I), I = (A D / pi)(1 - cos phi), phi = pi (rho - rho1)/D clamped to [0, 2 pi]
         const T PI = T(3.14159265358979323846);
@@ -319,6 +326,13 @@ struct AuxLayout {
 
 __device__ __forceinline__ long long gtid() { return blockIdx.x * (long long)blockDim.x + threadIdx.x; }
 
+// Block coordinates of a kernel body: blockIdx for a launch over one simulation, or the block
+// a batched launch assigned to this pass over its work list.
+struct Blk {
+    int x, y, z;
+};
+__device__ __forceinline__ Blk launch_blk() { return Blk{int(blockIdx.x), int(blockIdx.y), int(blockIdx.z)}; }
+
 template <typename T>
 __device__ __forceinline__ const T* cp(const void* v) { return static_cast<const T*>(v); }
 template <typename T>
@@ -396,7 +410,7 @@ __device__ __forceinline__ void block_max2(double a, double b, unsigned long lon
 // S1: moments and the c_s^2 window check
 // ---------------------------------------------------------------------------
 template <int LAT, typename T, int S, typename U>
-__global__ void __launch_bounds__(256, 3) k_moments(DevSim p, int src, int pair)
+__device__ __forceinline__ void b_moments(const DevSim& p, int src, int pair, const Blk bid)
 {
     using L = Lat<LAT>;
     using C = Codec<S>;
@@ -405,13 +419,13 @@ __global__ void __launch_bounds__(256, 3) k_moments(DevSim p, int src, int pair)
     int x = 0, y = 0, z = 0;
     long long s0;
     if (C::LOC) {
-        x = int(blockIdx.x * blockDim.x + threadIdx.x);
-        y = int(blockIdx.y);
-        z = int(blockIdx.z);
+        x = int(bid.x * blockDim.x + threadIdx.x);
+        y = bid.y;
+        z = bid.z;
         s0 = x < p.nx ? at(p, x, y, z) : p.N;
         x = min(x, p.nx - 1);
     } else {
-        s0 = gtid();
+        s0 = bid.x * (long long)blockDim.x + threadIdx.x;
     }
     const long long s = s0 < p.N ? s0 : (C::LOC ? at(p, x, y, z) : p.N - 1);  // tails recompute a site
     const bool own = s0 < p.N;
@@ -509,7 +523,7 @@ __global__ void __launch_bounds__(256, 3) k_moments(DevSim p, int src, int pair)
             for (int w = 1; w < int(blockDim.x >> 5); ++w) { lo = fminf(lo, slo[w]); hi = fmaxf(hi, shi[w]); }
             if (lo > 0.f) {
                 unsigned* rg = p.range + pair * 2 * kRangeSlots;
-                const int slot = blockIdx.x % kRangeSlots;
+                const int slot = (bid.x + bid.y + bid.z) % kRangeSlots;
                 atomicMin(rg + slot, __float_as_uint(lo));
                 atomicMax(rg + kRangeSlots + slot, __float_as_uint(hi));
             }
@@ -518,6 +532,11 @@ __global__ void __launch_bounds__(256, 3) k_moments(DevSim p, int src, int pair)
     const T cs2 = eos_p(p, r) / r;
     if (!isfinite(r)) atomicOr(p.status, STB_NONFINITE_RHO);
     else if (!(cs2 > phys<T>(p).cs2_lo && cs2 < phys<T>(p).cs2_hi)) atomicOr(p.status, STB_WEIGHTS);
+}
+template <int LAT, typename T, int S, typename U>
+__global__ void __launch_bounds__(256, 3) k_moments(DevSim p, int src, int pair)
+{
+    b_moments<LAT, T, S, U>(p, src, pair, launch_blk());
 }
 
 // ---------------------------------------------------------------------------
@@ -533,7 +552,7 @@ static __device__ double frozen_gain(const DevSim& p, double rho)
     return p.d * p.s2max / 12.0 * fmax(3.0 * cs2 - DP, cs2);
 }
 
-static __global__ void k_us_begin(DevSim p, int pair)
+static __device__ void b_us_begin(const DevSim& p, int pair)
 {
     UsolveState& u = p.us[pair];
     // spectrum bound g of this solve from the density range of the state, with 5 % margin
@@ -570,9 +589,11 @@ static __global__ void k_us_begin(DevSim p, int pair)
         u.c2 = p.omega > 0.0 ? p.omega : 2.0 / (2.0 - g);
     }
 }
+static __global__ void k_us_begin(DevSim p, int pair) { b_us_begin(p, pair); }
 
 // One thread: the S6 test, the S7 swap, and the loop condition of the graph.
-static __global__ void k_us_ctl(DevSim p, int pair, cudaGraphConditionalHandle h, int use_cond)
+// Returns whether the solve stopped.
+static __device__ bool b_us_ctl(const DevSim& p, int pair)
 {
     UsolveState& u = p.us[pair];
     const double r = __longlong_as_double((long long)u.resid_bits);
@@ -608,6 +629,11 @@ static __global__ void k_us_ctl(DevSim p, int pair, cudaGraphConditionalHandle h
         u.converged = conv ? 1 : 0;
         u.running = 0;
     }
+    return stop;
+}
+static __global__ void k_us_ctl(DevSim p, int pair, cudaGraphConditionalHandle h, int use_cond)
+{
+    const bool stop = b_us_ctl(p, pair);
     if (use_cond) cudaGraphSetConditional(h, stop ? 0u : 1u);
 }
 
@@ -1000,6 +1026,67 @@ __device__ __forceinline__ void prefetch_l2(const void* p) { asm volatile("prefe
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// ---------------------------------------------------------------------------
+// Tensor-memory-access (TMA) plane loads completed on shared-memory mbarriers.
+// One thread arms a ring slot's barrier with the bytes it expects and issues the
+// tensor copies; every thread then waits on the barrier's phase.  The waits are
+// bounded (about a second of clock), so a copy that never lands ends the kernel
+// with an error bit instead of a hang.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* q) { return static_cast<unsigned>(__cvta_generic_to_shared(q)); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// the barrier initialisation visible to the tensor copies (async proxy)
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory"); }
+// shared-memory accesses of the threads ordered before later tensor copies into the same bytes
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred P;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, P;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Wait for the phase of the given parity to complete; false after about 2^31 clocks.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > (1ll << 31)) return false;
+    return true;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, unsigned long long* bar, int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, unsigned long long* bar, int x, int y, int z,
+                                            int w)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], [%2];\n" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<unsigned long long>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "r"(w)
+        : "memory");
+}
+
 // Two consecutive shared-memory elements in one access (the index must be even).
 template <typename U>
 struct Vec2;
@@ -1038,7 +1125,8 @@ struct SweepPlan {
     static constexpr int R = D == 3 ? 5 + PF : 1;  // ring planes
     static constexpr int NQB = D == 3 ? 2 : 1;     // q plane buffers
     static constexpr size_t OFF_Q = size_t(R) * D * UP * sizeof(U);
-    static constexpr size_t OFF_R = (OFF_Q + size_t(NQB) * NQ * QP * sizeof(U) + 15) / 16 * 16;
+    // 128-byte aligned: the rho planes are tensor-copy destinations
+    static constexpr size_t OFF_R = (OFF_Q + size_t(NQB) * NQ * QP * sizeof(U) + 127) / 128 * 128;
     static constexpr size_t BYTES = OFF_R + size_t(R) * UP * sizeof(T);
 };
 
@@ -1054,8 +1142,12 @@ struct SweepPlan {
 //   stage Q  q_ab of plane zq = zl - 2 (in-plane halo 2; the z derivatives read the ring)
 //            into the other of the two q plane buffers.
 // In 2D the march is the single plane: stage Q in the first phase, stage J in the second.
-template <int LAT, typename T, typename U>
-__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2 : 1) k_sweep(DevSim p, int pair)
+// Plane loads: per-thread cp.async copies.  The TMA form (3D only) instead loads each plane of u
+// and rho - rho0 of a tile whose halo box lies inside the lattice in x and y with tensor copies
+// into the ring, one thread issuing them and an mbarrier per ring slot tracking them; tiles on the
+// periodic seams, whose boxes wrap, still copy per thread.  Both forms give identical results.
+template <int LAT, typename T, typename U, bool TMA>
+__device__ __forceinline__ void b_sweep(const DevSim& p, int pair, const Blk bid)
 {
     using L = Lat<LAT>;
     constexpr int D = L::D;
@@ -1067,14 +1159,15 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2
     constexpr int PF = SP::PF, R = SP::R;
     constexpr int HZ = D == 3 ? 4 : 0;
     static_assert(TX * TY == NT, "one J site per thread");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) unsigned long long ring_bar[SP::R];  // one per ring slot (TMA)
     U* su = reinterpret_cast<U*>(smem_raw);             // [R][D][UP]: u
     U* sq = reinterpret_cast<U*>(smem_raw + SP::OFF_Q);  // [NQB][NQ][QP]: q_ab
     T* sr = reinterpret_cast<T*>(smem_raw + SP::OFF_R);  // [R][UP]: rho - rho0
     auto slot = [](int z) { return D == 3 ? (z + 8 * R) % R : 0; };  // z >= -8
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
+    const int x0 = bid.x * TX, y0 = bid.y * TY;
+    const int z0 = D == 3 ? bid.z * TL::ZB : 0;
     const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
     const long long NP = (long long)p.nx * p.ny;  // sites per plane
     const T* drho = cp<T>(p.rho);
@@ -1133,6 +1226,36 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2
             }
         }
     };
+    // Tensor copies for tiles whose halo box stays inside the lattice in x and y (CTA-uniform).
+    // The box starts at x0 - 4, a multiple of 4 sites, as a tensor copy requires.
+    bool tma = false;
+    if constexpr (D == 3 && TMA) {
+        tma = p.tma != 0 && x0 >= 4 && x0 + TX + 4 <= p.nx && y0 >= 4 && y0 + TY + 4 <= p.ny &&
+              (smem_u32(smem_raw) & 127u) == 0;
+        if (tma) {
+            if (tid == 0) {
+#pragma unroll
+                for (int k = 0; k < R; ++k) mbar_init(&ring_bar[k], 1);
+                fence_mbar_init();
+            }
+            __syncthreads();
+        }
+    }
+    unsigned phase = 0;  // parity of each ring slot's barrier phase that the next wait expects
+    int aborted_at = INT_MIN;  // plane whose tensor copies timed out
+    auto fetch_tma = [&](int zl) {
+        if (tid == 0) {
+            const int sl = slot(zl);
+            const int zz = wrapc(zl, p.nz);
+            unsigned long long* bar = &ring_bar[sl];
+            fence_proxy_async_smem();
+            mbar_expect_tx(bar, unsigned(D * UP * sizeof(U) + UP * sizeof(T)));
+            const CUtensorMap* um = &p.tmaps->u[pair][cur];
+#pragma unroll
+            for (int a = 0; a < D; ++a) tma_load_4d(su + (sl * D + a) * UP, um, bar, x0 - 4, y0 - 4, zz, a);
+            tma_load_3d(sr + sl * UP, &p.tmaps->rho, bar, x0 - 4, y0 - 4, zz);
+        }
+    };
     // stage J inputs of the own site (j0', previous update), fetched one plane ahead
     U pj[3] = {U(0), U(0), U(0)}, pd[3] = {U(0), U(0), U(0)};
     auto fetch_j = [&](int zj) {
@@ -1154,7 +1277,8 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2
     U ju[3] = {U(0), U(0), U(0)}, jr = U(0);  // own u and rho - rho0 of the plane being finished
 #pragma unroll
     for (int k = 0; k < PF; ++k) {
-        fetch(z0 - HZ + k);
+        if (tma) fetch_tma(z0 - HZ + k);
+        else fetch(z0 - HZ + k);
         cp_async_commit();
     }
     fetch_j(z0);
@@ -1170,12 +1294,30 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2
             if (zl < z1 + HZ) fetch(zl);
             cp_async_commit();
         }
-        cp_async_wait<PF == 0 ? 0 : PF - 1>();  // plane zl has landed (this thread's copies)
-        __syncthreads();                         // ... and everyone's; the previous phase is done
+        bool late = false;
+        if (tma) {  // plane zl's tensor copies have landed
+            const int sl = slot(zl);
+            late = !mbar_wait(&ring_bar[sl], (phase >> sl) & 1u);
+            if (!late) phase ^= 1u << sl;
+        } else {
+            cp_async_wait<PF == 0 ? 0 : PF - 1>();  // plane zl has landed (this thread's copies)
+        }
+        // ... and everyone's copies; the previous phase is done
+        if (!tma) {
+            __syncthreads();
+        } else if (__syncthreads_or(late)) {
+            // a tensor copy did not land in time: record it and stop the solve (below, once the
+            // copies still in flight, planes zl .. zl + PF - 1, have landed or timed out)
+            aborted_at = zl;
+            break;
+        }
         // The ring slot of plane zl + PF held plane zl + PF - R = zl - 5, which only the previous
         // phase read.
         if (PF > 0) {
-            if (zl + PF < z1 + HZ) fetch(zl + PF);
+            if (zl + PF < z1 + HZ) {
+                if (tma) fetch_tma(zl + PF);
+                else fetch(zl + PF);
+            }
             cp_async_commit();
         }
         const int zq = zl - HZ / 2, zs = zq - 1;
@@ -1302,9 +1444,22 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2
         }
     }
     cp_async_wait<0>();
+    if (aborted_at != INT_MIN) {
+        if (tid == 0) {
+            atomicOr(p.status, STB_TIMEOUT);
+            for (int z = aborted_at; z < aborted_at + PF && z < z1 + HZ; ++z)
+                (void)mbar_wait(&ring_bar[slot(z)], (phase >> slot(z)) & 1u);
+        }
+        bad = true;  // the residual reads as infinite: the control kernel ends the solve
+    }
     // NaN -> +inf, which orders above every finite residual
     const double dmax_d = bad ? __longlong_as_double(0x7ff0000000000000ll) : double(dmax);
     block_max2(dmax_d, double(jmax), &p.us[pair].resid_bits, &p.us[pair].jmax_bits);
+}
+template <int LAT, typename T, typename U, bool TMA>
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2 : 1) k_sweep(DevSim p, int pair)
+{
+    b_sweep<LAT, T, U, TMA>(p, pair, launch_blk());
 }
 
 // S2 (tiled): f = kappa rho d_a lap rho with the third-derivative stencil of Sec. IV.E,
@@ -1321,7 +1476,7 @@ struct ForcePlan {
 };
 
 template <int LAT, typename T, typename U>
-__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_force(DevSim p, int pair)
+__device__ __forceinline__ void b_force(const DevSim& p, int pair, const Blk bid)
 {
     using L = Lat<LAT>;
     constexpr int D = L::D;
@@ -1334,8 +1489,8 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_force(DevSim p, 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sr = reinterpret_cast<T*>(smem_raw);  // [R][RY][RX]: rho - rho0
     const int tid = threadIdx.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
+    const int x0 = bid.x * TX, y0 = bid.y * TY;
+    const int z0 = D == 3 ? bid.z * TL::ZB : 0;
     const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
     const long long NP = (long long)p.nx * p.ny;
     const T* drho = cp<T>(p.rho);
@@ -1440,12 +1595,17 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_force(DevSim p, 
         if (zc >= z0 && zc < z1) fetch_own(zc + 1);
     }
 }
+template <int LAT, typename T, typename U>
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) k_force(DevSim p, int pair)
+{
+    b_force<LAT, T, U>(p, pair, launch_blk());
+}
 
 // S8 and S10 (tiled): the pointwise rho, u, p of every plane go to the ring
 // (halo 2); the first derivatives of u, j = rho u, p, p/rho and p u_b u_c
 // at the tile's sites feed derivs_tail.
 template <int LAT, typename T, typename U>
-__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim p)
+__device__ __forceinline__ void b_derivs(const DevSim& p, const Blk bid)
 {
     using L = Lat<LAT>;
     constexpr int D = L::D;
@@ -1456,8 +1616,8 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sr = reinterpret_cast<T*>(smem_raw);  // [R][NP][RY][RX]
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
+    const int x0 = bid.x * TX, y0 = bid.y * TY;
+    const int z0 = D == 3 ? bid.z * TL::ZB : 0;
     const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
     const T* drho = cp<T>(p.rho);
     const T* j0p = cp<T>(p.j0p);
@@ -1557,6 +1717,11 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
         if (DerivsPlan<D, T>::CLOSING_BARRIER) __syncthreads();
     }
 }
+template <int LAT, typename T, typename U>
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim p)
+{
+    b_derivs<LAT, T, U>(p, launch_blk());
+}
 
 // Ring of the collision kernel: the 5 planes of the derivative stencil and PF planes in flight;
 // the copy into the next slot starts after the plane's barrier (one barrier per plane).
@@ -1577,7 +1742,7 @@ struct CollidePlan {
 // d_a A, d_g B_ag and d_a C_b at the tile's sites complete Sigma; collide_tail
 // then collides and streams.
 template <int LAT, typename T, int S, typename U, bool READ>
-__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSim p, int src)
+__device__ __forceinline__ void b_collide(const DevSim& p, int src, const Blk bid)
 {
     using L = Lat<LAT>;
     constexpr int D = L::D;
@@ -1589,8 +1754,8 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sr = reinterpret_cast<T*>(smem_raw);  // [R][NP][RY][RX]
     const int tid = threadIdx.x, nth = blockDim.x;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
+    const int x0 = bid.x * TX, y0 = bid.y * TY;
+    const int z0 = D == 3 ? bid.z * TL::ZB : 0;
     const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
     const T* aux = cp<T>(p.aux);
     const T* drho = cp<T>(p.rho);
@@ -1744,6 +1909,126 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSi
                 collide_tail<LAT, T, S, READ>(p, src, r, drs, u, f, jtl, Sig, Xi);
             }
         }
+    }
+}
+template <int LAT, typename T, int S, typename U, bool READ>
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_collide(DevSim p, int src)
+{
+    b_collide<LAT, T, S, U, READ>(p, src, launch_blk());
+}
+
+// ---------------------------------------------------------------------------
+// Batched forms of the step kernels.  A persistent grid walks the work list of every
+// simulation in the table: pass `item` is block (or tile) item - start[k] of slot k.  Slots
+// that do not take this step, and in the u-solve those whose solve has stopped, are skipped.
+// Every block runs the same body as the one-simulation launch, so each simulation's result
+// is bitwise the one it gets alone.
+// ---------------------------------------------------------------------------
+// slot holding work item `item` in the prefix table start[0..n] (a short scan: n <= 32)
+__device__ __forceinline__ int batch_slot(const int* start, int n, int item)
+{
+    int k = 0;
+    while (k + 1 < n && start[k + 1] <= item) ++k;
+    return k;
+}
+
+static __global__ void kb_step_begin(const DevSim* sims, BatchWork* w)
+{
+    const int k = threadIdx.x;
+    if (k < kBatchSlots) w->live[k] = (k < w->nslot && w->todo[k] > 0) ? 1 : 0;
+}
+
+static __global__ void kb_step_end(const DevSim* sims, BatchWork* w)
+{
+    const int k = threadIdx.x;
+    if (k < kBatchSlots && w->live[k]) {
+        w->src[k] ^= 1;
+        w->todo[k] -= 1;
+    }
+}
+
+template <int LAT, typename T, int S, typename U>
+__global__ void __launch_bounds__(256, 3) kb_moments(const DevSim* sims, const BatchWork* w, int pair)
+{
+    const int n = w->nslot, total = w->mstart[n];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int k = batch_slot(w->mstart, n, item);
+        if (!w->live[k]) continue;
+        const int b = item - w->mstart[k], gx = w->mgx[k], gy = w->mgy[k];
+        b_moments<LAT, T, S, U>(sims[k], w->src[k], pair, Blk{b % gx, (b / gx) % gy, b / (gx * gy)});
+        __syncthreads();
+    }
+}
+
+// tile coordinates of tile b of slot k
+__device__ __forceinline__ Blk batch_tile(const BatchWork* w, int k, int b)
+{
+    const int gx = w->tgx[k], gy = w->tgy[k];
+    return Blk{b % gx, (b / gx) % gy, b / (gx * gy)};
+}
+
+template <int LAT, typename T, typename U>
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) kb_force(const DevSim* sims, const BatchWork* w, int pair)
+{
+    const int n = w->nslot, total = w->tstart[n];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int k = batch_slot(w->tstart, n, item);
+        if (!w->live[k]) continue;
+        b_force<LAT, T, U>(sims[k], pair, batch_tile(w, k, item - w->tstart[k]));
+        __syncthreads();
+    }
+}
+
+static __global__ void kb_us_begin(const DevSim* sims, const BatchWork* w, int pair)
+{
+    const int k = threadIdx.x;
+    if (k < w->nslot && w->live[k]) b_us_begin(sims[k], pair);
+}
+
+template <int LAT, typename T, typename U>
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2 : 1)
+    kb_sweep(const DevSim* sims, const BatchWork* w, int pair)
+{
+    const int n = w->nslot, total = w->tstart[n];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int k = batch_slot(w->tstart, n, item);
+        if (!w->live[k] || !sims[k].us[pair].running) continue;
+        b_sweep<LAT, T, U, false>(sims[k], pair, batch_tile(w, k, item - w->tstart[k]));
+        __syncthreads();
+    }
+}
+
+// One warp: the control step of every slot whose solve is running; the loop goes on while any is.
+static __global__ void kb_us_ctl(const DevSim* sims, const BatchWork* w, int pair, cudaGraphConditionalHandle h)
+{
+    const int k = threadIdx.x;
+    bool still = false;
+    if (k < w->nslot && w->live[k] && sims[k].us[pair].running) still = !b_us_ctl(sims[k], pair);
+    const bool any = __any_sync(0xffffffffu, still);
+    if (k == 0) cudaGraphSetConditional(h, any ? 1u : 0u);
+}
+
+template <int LAT, typename T, typename U>
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) kb_derivs(const DevSim* sims, const BatchWork* w)
+{
+    const int n = w->nslot, total = w->tstart[n];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int k = batch_slot(w->tstart, n, item);
+        if (!w->live[k]) continue;
+        b_derivs<LAT, T, U>(sims[k], batch_tile(w, k, item - w->tstart[k]));
+        __syncthreads();
+    }
+}
+
+template <int LAT, typename T, int S, typename U, bool READ>
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) kb_collide(const DevSim* sims, const BatchWork* w)
+{
+    const int n = w->nslot, total = w->tstart[n];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int k = batch_slot(w->tstart, n, item);
+        if (!w->live[k]) continue;
+        b_collide<LAT, T, S, U, READ>(sims[k], w->src[k], batch_tile(w, k, item - w->tstart[k]));
+        __syncthreads();
     }
 }
 
@@ -1964,7 +2249,8 @@ KernelTable make_table(bool read_pops)
     t.moments = (const void*)k_moments<LAT, T, S, U>;
     t.force = (const void*)k_force<LAT, T, U>;
     t.us_begin = (const void*)k_us_begin;
-    t.sweep = (const void*)k_sweep<LAT, T, U>;
+    t.sweep = (const void*)k_sweep<LAT, T, U, false>;
+    t.sweep_tma = Lat<LAT>::D == 3 ? (const void*)k_sweep<LAT, T, U, true> : nullptr;
     t.us_ctl = (const void*)k_us_ctl;
     t.derivs = (const void*)k_derivs<LAT, T, U>;
     t.collide = read_pops ? (const void*)k_collide<LAT, T, S, U, true> : (const void*)k_collide<LAT, T, S, U, false>;
@@ -1977,6 +2263,15 @@ KernelTable make_table(bool read_pops)
     t.pops_in = (const void*)k_pops_in<LAT, S>;
     t.red_partial = (const void*)k_red_partial<LAT, S>;
     t.red_final = (const void*)k_red_final;
+    t.kb_step_begin = (const void*)kb_step_begin;
+    t.kb_moments = (const void*)kb_moments<LAT, T, S, U>;
+    t.kb_force = (const void*)kb_force<LAT, T, U>;
+    t.kb_us_begin = (const void*)kb_us_begin;
+    t.kb_sweep = (const void*)kb_sweep<LAT, T, U>;
+    t.kb_us_ctl = (const void*)kb_us_ctl;
+    t.kb_derivs = (const void*)kb_derivs<LAT, T, U>;
+    t.kb_collide = read_pops ? (const void*)kb_collide<LAT, T, S, U, true> : (const void*)kb_collide<LAT, T, S, U, false>;
+    t.kb_step_end = (const void*)kb_step_end;
     t.block = 256;
     using TL = Tile<Lat<LAT>::D>;
     t.tile[0] = TL::TX;
@@ -1985,13 +2280,20 @@ KernelTable make_table(bool read_pops)
     t.tile_threads = TL::THREADS;
     constexpr int D = Lat<LAT>::D;
     t.smem_sweep = SweepPlan<D, T, U>::BYTES;
+    t.sweep_box[0] = SweepPlan<D, T, U>::UX;
+    t.sweep_box[1] = SweepPlan<D, T, U>::UY;
     t.smem_force = size_t(ForcePlan<D>::R) * ForcePlan<D>::RP * sizeof(T);
     t.smem_derivs = size_t(DerivsPlan<D, T>::R) * 6 * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
     t.smem_collide = size_t(CollidePlan<D>::R) * (1 + AuxLayout<D>::NB + D) * (TL::TX + 4) * (TL::TY + 4) * sizeof(T);
     cudaFuncSetAttribute(t.force, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_force));
     cudaFuncSetAttribute(t.sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_sweep));
+    if (t.sweep_tma) cudaFuncSetAttribute(t.sweep_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_sweep));
     cudaFuncSetAttribute(t.derivs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_derivs));
     cudaFuncSetAttribute(t.collide, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_collide));
+    cudaFuncSetAttribute(t.kb_force, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_force));
+    cudaFuncSetAttribute(t.kb_sweep, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_sweep));
+    cudaFuncSetAttribute(t.kb_derivs, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_derivs));
+    cudaFuncSetAttribute(t.kb_collide, cudaFuncAttributeMaxDynamicSharedMemorySize, int(t.smem_collide));
     t.tsize = sizeof(T);
     t.usize = sizeof(U);
     t.ssize = sizeof(typename Codec<S>::type);

@@ -67,7 +67,8 @@ class lbm_request_result(ctypes.Structure):
 
 
 class lbm_serve_config(ctypes.Structure):
-    _fields_ = [("memory_budget", ctypes.c_size_t), ("max_active", ctypes.c_int), ("chunk_steps", ctypes.c_int)]
+    _fields_ = [("memory_budget", ctypes.c_size_t), ("max_active", ctypes.c_int), ("chunk_steps", ctypes.c_int),
+                ("batched", ctypes.c_int)]
 
 
 class LbmError(RuntimeError):
@@ -240,8 +241,10 @@ def lbm_moment_sums_noalloc(lattice, pops, n_sites, sums, stream=None):
     _check(rc, "lbm_moment_sums_noalloc")
 
 
-def lbm_serve(requests, memory_budget=0, max_active=16, chunk_steps=50):
+def lbm_serve(requests, memory_budget=0, max_active=16, chunk_steps=50, batched=1):
     """Run request dicts to completion (continuous batching); returns lbm_request_result[n].
+
+    batched = 1: batched launches per kernel combination; 0: one stream per simulation.
 
     Each dict has lattice, dims, eos (lbm_eos), params (lbm_params), steps, arrival_s,
     rho_init (C-contiguous float64 host array) and optionally u_init, rho_out, u_out
@@ -266,7 +269,7 @@ def lbm_serve(requests, memory_budget=0, max_active=16, chunk_steps=50):
                 keep.append(a)
                 setattr(q, name, ptr)
     out = (lbm_request_result * max(n, 1))()
-    cfg = lbm_serve_config(int(memory_budget), int(max_active), int(chunk_steps))
+    cfg = lbm_serve_config(int(memory_budget), int(max_active), int(chunk_steps), int(batched))
     _check(load_library().lbm_serve(reqs, n, ctypes.byref(cfg), out), "lbm_serve")
     return list(out)[:n]
 

@@ -39,21 +39,28 @@ def latency_stats(results, dicts):
             "mlups": work / span / 1e6 if span > 0 else None, "span_s": span}
 
 
-def run(n=256, load=0.8, max_active=16, chunk_steps=50, memory_budget=0, calibrate=24, seed=1):
+def run(n=256, load=0.8, max_active=16, chunk_steps=50, memory_budget=0, calibrate=24, seed=1, batched=1,
+        rate=None):
     """The serving workload: calibrate the batched throughput on the first `calibrate`
     requests (all present at t = 0), then replay the first n requests with Poisson arrivals
-    at `load` times that throughput (in site updates per second)."""
+    at `load` times that throughput (in site updates per second).  batched selects lbm_serve's
+    batched launches (1) or one stream per simulation (0); a given `rate` (requests per second)
+    replaces the calibrated one, so that two modes can replay the same arrivals."""
     reqs = W.serving_requests(n=n, seed=seed, rate=1.0)
     m = min(calibrate, n)
     cal = request_dicts(reqs[:m], time_scale=0.0)
-    res = P.lbm_serve(cal, memory_budget=memory_budget, max_active=max_active, chunk_steps=chunk_steps)
+    res = P.lbm_serve(cal, memory_budget=memory_budget, max_active=max_active, chunk_steps=chunk_steps,
+                      batched=batched)
     cal_stats = latency_stats(res, cal)
     thr = cal_stats["mlups"] * 1e6  # site updates per second, all requests resident
     mean_work = np.mean([r.side ** (2 if r.lattice == P.LBM_D2Q21 else 3) * r.steps for r in reqs])
-    rate = load * thr / mean_work  # requests per second
+    if rate is None:
+        rate = load * thr / mean_work  # requests per second
     dicts = request_dicts(reqs, time_scale=1.0 / rate)
-    res = P.lbm_serve(dicts, memory_budget=memory_budget, max_active=max_active, chunk_steps=chunk_steps)
+    res = P.lbm_serve(dicts, memory_budget=memory_budget, max_active=max_active, chunk_steps=chunk_steps,
+                      batched=batched)
     st = latency_stats(res, dicts)
     st.update({"calibration_mlups": cal_stats["mlups"], "calibration_requests": m, "arrival_rate_per_s": rate,
-               "offered_load": load, "max_active": max_active, "chunk_steps": chunk_steps})
+               "offered_load": load, "max_active": max_active, "chunk_steps": chunk_steps,
+               "mode": "batched launches per kernel combination" if batched else "one stream per simulation"})
     return st, res, dicts

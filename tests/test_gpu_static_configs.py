@@ -1,0 +1,94 @@
+"""The static configurations at their stated size, FP32 against FP64 after 1000 steps, and the
+256^3 spinodal over the 100 compared steps.
+
+The FP64 reference at these sizes is the library's own FP64 path (storage F64); the oracle
+cannot run 1000 steps of 2 million sites in minutes.  The FP64 path itself is compared with
+the oracle element by element on each full-size state for the steps the oracle finishes in
+seconds (all host threads), and on every smaller case in test_gpu_parity.py.
+
+Bounds:
+  * rho: 1e-6 relative L-infinity after 1000 steps (512^2 disc, 128^3 sphere) and after 100
+    steps of the spinodal, for FP32 deviation storage with the u-solve settings of the
+    benchmark (Chebyshev-accelerated FP32 sweeps) and of the plain iteration.
+  * u: on the scale max(|u_ref|, 1e-3 c_s(rho0)) (the static cases have |u| ~ 1e-4, the spurious
+    current).  A moving population deviation of ~1e-2 is stored to 2^-24 of itself, ~6e-10,
+    and j0 = sum_i c_i n_i sums 58 of them with |c| up to 4, so j0 (and u) carries ~1e-8 of
+    rounding each step: 1.4e-5 of the scale 7e-4.  Measured: 4e-5 (3D), 1.7e-4 (2D).  The
+    bounds are 2e-4 (3D) and 5e-4 (2D); 1e-6 on this scale is below what FP32 populations
+    resolve.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import paper_1402_2920_gb300 as P
+from oracle import oracle as O
+from paper_1402_2920_gb300 import workloads as W
+from tests.gpu_util import lib_sim, oracle_sim, perm_to_oracle, rel_linf, u_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(case, steps, storage, **kw):
+    g = lib_sim(case, storage=storage, **kw)
+    g.init(case.rho, case.u)
+    g.step(steps)
+    rho, u = g.fields()
+    st = g.stats()
+    g.close()
+    assert st.status == 0
+    return rho, u, st
+
+
+def _fp64_vs_oracle(case, steps):
+    """The FP64 path against the oracle on the full-size state, population by population."""
+    O.set_num_threads(os.cpu_count() or 1)
+    try:
+        g = lib_sim(case, storage=P.LBM_STORE_F64)
+        o = oracle_sim(case)
+        g.init(case.rho, case.u)
+        o.init(case.rho, case.u)
+        g.step(steps)
+        assert o.step(steps) == 0
+        idx = perm_to_oracle(case.lattice)
+        err = rel_linf(g.populations()[idx], o.pops())
+        g.close()
+    finally:
+        O.set_num_threads(1)
+    return err
+
+
+def _cs0(case):
+    return case.eos.T / (1 - case.eos.b * case.rho0) - case.eos.a * case.rho0
+
+
+BENCH = dict(omega=0.0, chebyshev=1)
+
+
+@pytest.mark.parametrize("name,steps_oracle,tol_u", [("droplet2d", 3, 5e-4), ("droplet3d", 1, 2e-4)])
+def test_static_droplet_fp32_vs_fp64_1000_steps(name, steps_oracle, tol_u):
+    """D2Q21 512^2 disc R = 64 and D3Q59 128^3 sphere R = 32, tanh width 4."""
+    case = W.make_case(name)
+    assert _fp64_vs_oracle(case, steps_oracle) < 1e-12
+    r64, u64, s64 = _run(case, 1000, P.LBM_STORE_F64)
+    for kw in ({}, BENCH):
+        r32, u32, s32 = _run(case, 1000, P.LBM_STORE_F32_DEV, **kw)
+        e_rho, e_u = rel_linf(r32, r64), u_err(u32, u64, _cs0(case))
+        print("%s 1000 steps %s: rho %.2e u %.2e" % (name, kw or "plain", e_rho, e_u))
+        assert e_rho < 1e-6
+        assert e_u < tol_u
+        assert abs(s32.mass - s64.mass) < 1e-11 * s64.mass
+
+
+def test_spinodal_256_fp32_vs_fp64_100_steps():
+    """The benchmark workload, D3Q59 256^3 spinodal, with the benchmark's settings."""
+    case = W.make_case("spinodal3d")
+    r64, u64, s64 = _run(case, 100, P.LBM_STORE_F64)
+    r32, u32, s32 = _run(case, 100, P.LBM_STORE_F32_DEV, **BENCH)
+    e_rho = rel_linf(r32, r64)
+    e_u = float(np.abs(u32 - u64).max() / np.abs(u64).max())
+    print("spinodal 256^3 100 steps: rho %.2e u %.2e (of max|u| %.2e)" % (e_rho, e_u, np.abs(u64).max()))
+    assert e_rho < 1e-6
+    assert e_u < 1e-4
+    assert abs(s32.mass - s64.mass) < 1e-11 * s64.mass
