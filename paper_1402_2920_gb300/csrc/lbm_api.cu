@@ -666,6 +666,8 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
         rc = rc ? rc : dev_alloc(s, &dv.pop0[0], N * s->kt.rsize);
         rc = rc ? rc : dev_alloc(s, &dv.pop0[1], N * s->kt.rsize);
     }
+    for (int b = 0; b < 2 && !rc; ++b)
+        for (int i = 0; i < s->Q; ++i) dv.popp[b][i] = static_cast<char*>(dv.pop[b]) + size_t(i) * N * SS;
     if (s->kt.exact) rc = rc ? rc : dev_alloc(s, &dv.rho_lo, N * sizeof(float));
     rc = rc ? rc : dev_alloc(s, &dv.rho, N * T);
     rc = rc ? rc : dev_alloc(s, &dv.j0p, 3 * N * T);

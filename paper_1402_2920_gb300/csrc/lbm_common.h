@@ -112,6 +112,9 @@ struct DevSim {
     Phys<double> pd;                 // and for FP64 arithmetic
     // Tensor maps of the sweep's plane loads (TMA) in device memory, valid when tma = 1.
     const struct SweepMaps* tmaps;
+    // plane i of population buffer b, pop[b] + i N elements: the collision's stores address their
+    // plane through this table (one parameter load instead of 64-bit index arithmetic per store)
+    void* popp[2][59];
     int tma;
 };
 
