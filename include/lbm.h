@@ -228,10 +228,13 @@ typedef struct {
     size_t memory_budget;   /* device bytes for simulations; 0: 90 % of free memory     */
     int max_active;         /* simulations resident at once                             */
     int chunk_steps;        /* steps issued to a simulation per turn of the loop        */
-    int batched;            /* 1: the resident simulations of each kernel combination (lattice,
-                               storage, u-solve precision, gamma = 0 or not) step together, one
-                               persistent launch per stage over all of them, at most 32 per
-                               combination; 0: one stream and one graph launch per simulation */
+    int batched;            /* 0: one stream and one graph launch per simulation; 1: the resident
+                               simulations of each kernel combination (lattice, storage, u-solve
+                               precision, gamma = 0 or not) and size class (sites within a factor
+                               of 4) step together, one persistent launch per stage over all of
+                               them, at most 32 per batch.  Both give the same results; on the
+                               seeded serving workload the per-stream form serves more site
+                               updates per second at lower latency                            */
 } lbm_serve_config;
 
 /* Run a stream of requests to completion on the current device (continuous batching).
@@ -278,6 +281,22 @@ const char* lbm_error_string(int code);
  *   stream do not.  Errors: LBM_E_INVALID_ARG (lattice, NULL pointer, n_sites out of
  *   range), LBM_E_CUDA (no device, launch failure). */
 int lbm_moment_sums_noalloc(int lattice, const double* pops, int64_t n_sites, double* sums, void* cuda_stream);
+
+/* Tensor cores for the collision's polynomial map, measured against the scalar form.
+ *   With gamma = 0 each post-collision population of D3Q59 is W_k P(c_i) + w_k(rho0) H(c_i)
+ *   (S11; n^eq of Sec. III, Delta^int and Delta^corr of Secs. VI and VIII), P and H polynomials
+ *   in c with 10 and 20 coefficients per site.  This times that map over n_sites synthetic
+ *   sites two ways: the scalar per-pair form the collision kernel uses, and one tcgen05 matrix
+ *   product per tile of 128 sites ([128 x 32] coefficients, split into two TF32 terms, times
+ *   the [32 x 128] table of monomials, accumulator in tensor memory).  Each form reduces a
+ *   site's 59 values to one weighted sum; the two sums are compared on the host.
+ *   n_sites: a multiple of 128, at most 2^31.  reps >= 1 timed repetitions after one warm-up.
+ *   Outputs (host): milliseconds per pass of each form, the largest difference of the two
+ *   per-site sums and the largest sum.  Allocates and frees its own device buffers; runs on
+ *   the legacy default stream and synchronises.  Errors: LBM_E_INVALID_ARG, LBM_E_OOM,
+ *   LBM_E_CUDA, LBM_E_TIMEOUT (a tensor-core completion wait ran out). */
+int lbm_collision_map_bench(int64_t n_sites, int reps, double* ms_scalar, double* ms_tensor, double* max_abs_diff,
+                            double* max_abs_value);
 
 /* Free a simulation and its device memory.  NULL is accepted. */
 void lbm_destroy(lbm_sim* sim);

@@ -1131,13 +1131,20 @@ struct Batch {
     cudaGraphExec_t x = nullptr;
 };
 
-int batch_key(int lattice, const lbm_params& prm)
+int batch_key(int lattice, const int64_t dims[3], const lbm_params& prm)
 {
     const bool us64 = prm.storage == LBM_STORE_F64 || prm.usolve_precision == LBM_USOLVE_F64;
-    return ((lattice * 16 + prm.storage) * 2 + (us64 ? 1 : 0)) * 2 + (prm.gamma != 0.0 ? 1 : 0);
+    const int combo = ((lattice * 16 + prm.storage) * 2 + (us64 ? 1 : 0)) * 2 + (prm.gamma != 0.0 ? 1 : 0);
+    int64_t n = dims[0] * dims[1] * (lattice == LBM_D3Q59 ? dims[2] : 1);
+    int size_class = 0;
+    while (n >= 4) {
+        n >>= 2;
+        ++size_class;
+    }
+    return combo * 64 + size_class;
 }
 
-int batch_key_of(const lbm_sim* s) { return batch_key(s->lattice, s->prm); }
+int batch_key_of(const lbm_sim* s) { return batch_key(s->lattice, s->dims, s->prm); }
 
 namespace {
 

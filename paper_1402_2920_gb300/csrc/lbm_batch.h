@@ -17,9 +17,10 @@ namespace lbm {
 
 struct Batch;
 
-// Kernel combination of a simulation with these parameters: simulations batch together only
-// when their keys are equal.
-int batch_key(int lattice, const lbm_params& prm);
+// Batch key of a simulation: its kernel combination and its size class (sites within a factor
+// of 4).  Simulations batch together only when their keys are equal: a batch steps in lockstep,
+// so a small simulation beside a much larger one would wait for it at every stage.
+int batch_key(int lattice, const int64_t dims[3], const lbm_params& prm);
 int batch_key_of(const lbm_sim* s);
 
 // A batch for the key of `proto` whose launches go to `stream`.

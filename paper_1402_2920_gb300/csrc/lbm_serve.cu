@@ -9,7 +9,7 @@
 //
 // Two ways of advancing the resident simulations:
 //   batched   the simulations of one kernel combination (lattice, storage, u-solve precision,
-//             gamma = 0 or not) form a batch whose chunk is one graph launch per step: each
+//             gamma = 0 or not) and size class form a batch whose chunk is one graph launch per step: each
 //             stage of the step is one persistent launch over the tiles of every simulation in
 //             the batch (lbm_batch.h).  A batch takes its next chunk once the previous one is
 //             done; waiting requests of that combination join in between.  Batches of
@@ -237,7 +237,7 @@ int serve_batched(const lbm_request* reqs, int n, const lbm_serve_config* cfg, l
                 continue;
             }
             if (used + bytes > budget) break;  // wait for memory
-            const int key = lbm::batch_key(r.lattice, r.params);
+            const int key = lbm::batch_key(r.lattice, r.dims, r.params);
             Family* f = nullptr;
             for (Family& g : fams)
                 if (g.key == key) f = &g;

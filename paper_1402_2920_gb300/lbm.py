@@ -27,7 +27,7 @@ LBM_E_OOM, LBM_E_CUDA, LBM_E_TIMEOUT, LBM_E_IO = -5, -6, -7, -8
 ENTRY_POINTS = ("lbm_create", "lbm_footprint_bytes", "lbm_init", "lbm_step", "lbm_fields", "lbm_populations",
                 "lbm_set_populations", "lbm_velocities", "lbm_stats_get", "lbm_sync", "lbm_save", "lbm_load",
                 "lbm_step_batch", "lbm_error_string", "lbm_destroy", "lbm_profile", "lbm_moment_sums_noalloc",
-                "lbm_serve")
+                "lbm_serve", "lbm_collision_map_bench")
 
 #: kernel order of lbm_profile
 PROFILE_STAGES = ("moments", "force", "usolve_sweep", "derivs", "collide")
@@ -107,6 +107,8 @@ def load_library(path=LIB_PATH):
     L.lbm_error_string.argtypes = [ctypes.c_int]
     L.lbm_error_string.restype = ctypes.c_char_p
     L.lbm_profile.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int]
+    dp = ctypes.POINTER(ctypes.c_double)
+    L.lbm_collision_map_bench.argtypes = [ctypes.c_int64, ctypes.c_int, dp, dp, dp, dp]
     L.lbm_destroy.argtypes = [vp]
     L.lbm_destroy.restype = None
     for name in ENTRY_POINTS:
@@ -241,10 +243,11 @@ def lbm_moment_sums_noalloc(lattice, pops, n_sites, sums, stream=None):
     _check(rc, "lbm_moment_sums_noalloc")
 
 
-def lbm_serve(requests, memory_budget=0, max_active=16, chunk_steps=50, batched=1):
+def lbm_serve(requests, memory_budget=0, max_active=16, chunk_steps=50, batched=0):
     """Run request dicts to completion (continuous batching); returns lbm_request_result[n].
 
-    batched = 1: batched launches per kernel combination; 0: one stream per simulation.
+    batched = 0: one stream per simulation (the faster on the seeded serving workload);
+    1: batched launches per kernel combination and size class.
 
     Each dict has lattice, dims, eos (lbm_eos), params (lbm_params), steps, arrival_s,
     rho_init (C-contiguous float64 host array) and optionally u_init, rho_out, u_out
@@ -279,6 +282,14 @@ def lbm_profile(sim, reps=10):
     out = (ctypes.c_double * len(PROFILE_STAGES))()
     _check(load_library().lbm_profile(ctypes.c_void_p(sim), int(reps), out, len(PROFILE_STAGES)), "lbm_profile")
     return dict(zip(PROFILE_STAGES, list(out)))
+
+
+def lbm_collision_map_bench(n_sites, reps=5):
+    """(ms scalar, ms tensor, max |difference|, max |value|) of the collision's polynomial map."""
+    v = [ctypes.c_double() for _ in range(4)]
+    _check(load_library().lbm_collision_map_bench(int(n_sites), int(reps), *[ctypes.byref(x) for x in v]),
+           "lbm_collision_map_bench")
+    return tuple(x.value for x in v)
 
 
 def lbm_step_batch(sims, nsteps):

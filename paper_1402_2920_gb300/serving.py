@@ -39,7 +39,7 @@ def latency_stats(results, dicts):
             "mlups": work / span / 1e6 if span > 0 else None, "span_s": span}
 
 
-def run(n=256, load=0.8, max_active=16, chunk_steps=50, memory_budget=0, calibrate=24, seed=1, batched=1,
+def run(n=256, load=0.8, max_active=16, chunk_steps=50, memory_budget=0, calibrate=24, seed=1, batched=0,
         rate=None):
     """The serving workload: calibrate the batched throughput on the first `calibrate`
     requests (all present at t = 0), then replay the first n requests with Poisson arrivals
