@@ -1161,7 +1161,7 @@ int resident_grid(const void* fn, int threads, size_t smem)
     return sms * per;
 }
 
-int build_batch_graph(Batch* b, int lattice)
+int build_batch_graph(Batch* b)
 {
     LBM_CK(cudaGraphCreate(&b->g, 0));
     const KernelTable& kt = b->kt;
@@ -1219,7 +1219,6 @@ int build_batch_graph(Batch* b, int lattice)
         void* a[] = {&sims, &w};
         LBM_CK(add_kernel(b->g, &n7, kt.kb_step_end, dim3(1), 32, a, &n6, 1));
     }
-    (void)lattice;
     LBM_CK(cudaGraphInstantiate(&b->x, b->g, 0));
     return LBM_OK;
 }
@@ -1249,7 +1248,7 @@ int batch_create(const lbm_sim* proto, cudaStream_t stream, Batch** out)
     if (!rc) {
         std::memset(static_cast<void*>(b->h_sims), 0, sizeof(DevSim) * kBatchSlots);
         std::memset(static_cast<void*>(b->h_work), 0, sizeof(BatchWork));
-        rc = build_batch_graph(b, proto->lattice);
+        rc = build_batch_graph(b);
     }
     if (rc) {
         batch_destroy(b);

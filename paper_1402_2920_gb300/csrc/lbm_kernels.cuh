@@ -1113,17 +1113,21 @@ __device__ __forceinline__ void st2(U* p, U a, U b)
 }
 
 // Shared-memory plan of the sweep: a ring of R planes of u (sweep precision) and rho - rho0
-// (storage precision) with in-plane halo 4, PF of them in flight, and the q planes, which
-// share the row pitch UX of the ring so that a warp's stage-Q reads fall in distinct banks.
+// (storage precision) with in-plane halo 4, PF of them in flight, and the q plane, which
+// shares the row pitch UX of the ring so that a warp's stage-Q reads fall in distinct banks.
+// One plane in flight and one q buffer keep the plan at 73 KB (FP32), so that three CTAs share
+// an SM: at 256^3 that is 0.412 ms per sweep against 0.430 ms for two CTAs with two planes in
+// flight and a double-buffered q (95 KB), whose single barrier per phase the second barrier
+// here gives back.
 template <int D, typename T, typename U>
 struct SweepPlan {
     using TL = Tile<D>;
     static constexpr int UX = TL::TX + 8, UY = TL::TY + 8, UP = UX * UY;
     static constexpr int QX = TL::TX + 4, QY = TL::TY + 4, QP = QY * UX;
     static constexpr int NQ = D == 3 ? 6 : 3;
-    static constexpr int PF = D == 3 ? 2 : 0;      // planes fetched ahead
+    static constexpr int PF = D == 3 ? 1 : 0;      // planes fetched ahead
     static constexpr int R = D == 3 ? 5 + PF : 1;  // ring planes
-    static constexpr int NQB = D == 3 ? 2 : 1;     // q plane buffers
+    static constexpr int NQB = 1;                  // q plane buffers
     static constexpr size_t OFF_Q = size_t(R) * D * UP * sizeof(U);
     // 128-byte aligned: the rho planes are tensor-copy destinations
     static constexpr size_t OFF_R = (OFF_Q + size_t(NQB) * NQ * QP * sizeof(U) + 127) / 128 * 128;
@@ -1131,7 +1135,7 @@ struct SweepPlan {
 };
 
 // S3-S6 fused: one sweep of the u-solve, iterated in u = (j0' + j~)/rho (the same iteration
-// as in j~, which the paper uses).  The CTA marches along z; per phase zl (one barrier):
+// as in j~, which the paper uses).  The CTA marches along z; per phase zl (two barriers):
 //   fetch    plane zl + PF of u and rho - rho0 (in-plane halo 4) into the ring, asynchronously;
 //   stage J  at the thread's own site, for the plane zs = zq - 1 that the previous phase's
 //            stage Q wrote: the in-plane part d_x q_ax + d_y q_ay of plane zs, and q_az(zs)
@@ -1139,8 +1143,8 @@ struct SweepPlan {
 //            registers.  Plane zs - 2 is then complete: j~new = -(1/12) d_b q_ab (S5),
 //            J(u) = (j0' + j~new)/rho, the update d = c1 d_prev + c2 (J(u) - u), u += d, and
 //            the S6 difference rho |d| = |j~new - j~| of the resulting j~ iterates;
-//   stage Q  q_ab of plane zq = zl - 2 (in-plane halo 2; the z derivatives read the ring)
-//            into the other of the two q plane buffers.
+//   stage Q  after a barrier (stage J's reads are done), q_ab of plane zq = zl - 2 (in-plane
+//            halo 2; the z derivatives read the ring) into the q plane buffer.
 // In 2D the march is the single plane: stage Q in the first phase, stage J in the second.
 // Plane loads: per-thread cp.async copies.  The TMA form (3D only) instead loads each plane of u
 // and rho - rho0 of a tile whose halo box lies inside the lattice in x and y with tensor copies
@@ -1282,11 +1286,11 @@ __device__ __forceinline__ void b_sweep(const DevSim& p, int pair, const Blk bid
         cp_async_commit();
     }
     fetch_j(z0);
-    // q_ab of plane z lives in one of two plane buffers
-    auto qbuf = [&](int z) { return sq + (D == 3 ? (z & 1) : 0) * NQ * QP; };
+    // q_ab of plane z lives in the q plane buffer (or one of two, with NQB = 2)
+    auto qbuf = [&](int z) { return sq + (SP::NQB == 2 ? (z & 1) : 0) * NQ * QP; };
     auto qplane = [&](int z) { return D == 2 ? z == 0 : (z >= z0 - 2 && z < z1 + 2); };
-    // Phase zl (one barrier): stage J of plane zs = zq - 1, from the q that the previous phase
-    // wrote, and stage Q of plane zq = zl - HZ/2 into the other q buffer.  The J stage of plane zs
+    // Phase zl: stage J of plane zs = zq - 1, from the q that the previous phase wrote, and stage Q
+    // of plane zq = zl - HZ/2 into the q buffer once J has read it.  The J stage of plane zs
     // finishes plane zs - 2 (3D), whose own u and rho - rho0 the previous phase read from the
     // ring; the last phase only finishes.
     for (int zl = z0 - HZ; zl < z1 + HZ + 1; ++zl) {
@@ -1394,6 +1398,7 @@ __device__ __forceinline__ void b_sweep(const DevSim& p, int pair, const Blk bid
             for (int a = 0; a < D; ++a) ju[a] = uc[a * UP + ui];
             jr = U(sr[slot(zj) * UP + ui]);
         }
+        if (SP::NQB == 1 && D == 3) __syncthreads();  // stage J's reads of the q plane are done
         if (qplane(zq)) {  // stage Q: plane zq, two x-neighbouring points per thread (64-bit reads)
             U* qb = qbuf(zq);
             const U* pl[5];
@@ -1457,7 +1462,7 @@ __device__ __forceinline__ void b_sweep(const DevSim& p, int pair, const Blk bid
     block_max2(dmax_d, double(jmax), &p.us[pair].resid_bits, &p.us[pair].jmax_bits);
 }
 template <int LAT, typename T, typename U, bool TMA>
-__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 2 : 1) k_sweep(DevSim p, int pair)
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(U) == 4 ? 3 : 1) k_sweep(DevSim p, int pair)
 {
     b_sweep<LAT, T, U, TMA>(p, pair, launch_blk());
 }

@@ -56,12 +56,12 @@ __device__ __forceinline__ float urand(unsigned& state)
 // Sigma and Xi' ~ 1e-4) and the monomial coefficients of P (a[0..9]) and H (a[10..29]).
 // Monomial order: 1, x, y, z, xx, yy, zz, xy, xz, yz (P and H), then xxx, yyy, zzz, xxy, xxz,
 // xyy, yyz, xzz, yzz, xyz (H).
-__device__ __forceinline__ void site_coeffs(const MapConst& c, long long s, float (&a)[30], float& W_rho, float& sc)
+__device__ __forceinline__ void site_coeffs(const MapConst& c, long long s, float (&a)[30], float& rho_out, float& sc)
 {
     unsigned st = hash32(unsigned(s) ^ hash32(unsigned(s >> 32) + 0x632be5abu));
     const float rho = c.rho0 + 0.1f * urand(st);
     sc = c.s0 + 0.05f * urand(st);
-    W_rho = rho;
+    rho_out = rho;
     float u[3], f[3], jt[3], S[6], X[10];
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
