@@ -688,6 +688,14 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
         rc = rc ? rc : dev_alloc(s, &dv.dvec[1], 3 * N * U);
     }
     rc = rc ? rc : dev_alloc(s, &dv.aux, size_t(MAX_AUX) * N * T);
+    if (!rc) {
+        for (int c = 0; c < MAX_AUX; ++c) dv.auxp[c] = static_cast<char*>(dv.aux) + size_t(c) * N * T;
+        for (int a = 0; a < 3; ++a) {
+            dv.j0pp[a] = static_cast<char*>(dv.j0p) + size_t(a) * N * T;
+            dv.fpp[a] = static_cast<char*>(dv.f) + size_t(a) * N * T;
+            dv.jwp[a] = static_cast<char*>(dv.jt_warm) + size_t(a) * N * U;
+        }
+    }
     void* usp = nullptr;
     rc = rc ? rc : dev_alloc(s, &usp, 2 * sizeof(UsolveState));
     dv.us = static_cast<UsolveState*>(usp);

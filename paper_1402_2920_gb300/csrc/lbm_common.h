@@ -115,6 +115,12 @@ struct DevSim {
     // plane i of population buffer b, pop[b] + i N elements: the collision's stores address their
     // plane through this table (one parameter load instead of 64-bit index arithmetic per store)
     void* popp[2][59];
+    // plane tables of the aux field (aux + c N) and of the 3-vector fields j0', f and the warm-start
+    // j~ (field + a N), in the field's element type
+    void* auxp[26];
+    void* j0pp[3];
+    void* fpp[3];
+    void* jwp[3];
     int tma;
 };
 

@@ -337,6 +337,12 @@ template <typename T>
 __device__ __forceinline__ const T* cp(const void* v) { return static_cast<const T*>(v); }
 template <typename T>
 __device__ __forceinline__ T* mp(void* v) { return static_cast<T*>(v); }
+// Plane c of the aux field and plane a of a 3-vector field, through the parameter block's tables
+// (one parameter load per access instead of 64-bit index arithmetic)
+template <typename T>
+__device__ __forceinline__ T* auxp(const DevSim& p, int c) { return static_cast<T*>(p.auxp[c]); }
+template <typename T>
+__device__ __forceinline__ T* plane(void* const (&tab)[3], int a) { return static_cast<T*>(tab[a]); }
 
 // Stored value of population i at site s of buffer b: n_i, or n_i - w_i(rho0) rho0.
 // The 16-bit storages keep the rest population (i = 0) in FP32 so that the mass
@@ -666,22 +672,21 @@ __device__ __forceinline__ void derivs_tail(const DevSim& p, long long s, const 
     for (int a = 0; a < D; ++a) divu += du[a][a];
     T k1, k2, k3;
     collision_consts<LAT, T>(p, k1, k2, k3);
-    T* aux = mp<T>(p.aux);
-    aux[AL::A * p.N + s] = PM * divu;
+    auxp<T>(p, AL::A)[s] = PM * divu;
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
         for (int b = a; b < D; ++b) {
             const T sd = du[a][b] + du[b][a];
-            aux[(AL::B + sym2<D>(a, b)) * p.N + s] = P * sd;
-            aux[(AL::SIGL + sym2<D>(a, b)) * p.N + s] = k2 * (-DP * divj * sd + (a == b ? RPP * divu * divj : T(0)));
+            auxp<T>(p, AL::B + sym2<D>(a, b))[s] = P * sd;
+            auxp<T>(p, AL::SIGL + sym2<D>(a, b))[s] = k2 * (-DP * divj * sd + (a == b ? RPP * divu * divj : T(0)));
         }
 #pragma unroll
     for (int b = 0; b < D; ++b) {
         T c = dp[b] / rs;
 #pragma unroll
         for (int g = 0; g < D; ++g) c += u[g] * du[g][b];
-        aux[(AL::C + b) * p.N + s] = c;
+        auxp<T>(p, AL::C + b)[s] = c;
     }
     // Xi'_abc = k3 [X(a,b;c) + X(a,c;b) + X(b,c;a)] + (1-gamma) cs0 (delta j~ sym),
     // X(a,b;c) = d_c(p u_a u_b) + delta_ab [p d_c(p/rho) + (p - rho p') u_c div u]
@@ -696,7 +701,7 @@ __device__ __forceinline__ void derivs_tail(const DevSim& p, long long s, const 
             for (int c = b; c < D; ++c) {
                 T v = k3 * (X(a, b, c) + X(a, c, b) + X(b, c, a));
                 v += cj * ((a == b ? jtl[c] : T(0)) + (a == c ? jtl[b] : T(0)) + (b == c ? jtl[a] : T(0)));
-                aux[(AL::XI + sym3<D>(a, b, c)) * p.N + s] = v;
+                auxp<T>(p, AL::XI + sym3<D>(a, b, c))[s] = v;
             }
 }
 
@@ -1175,7 +1180,6 @@ __device__ __forceinline__ void b_sweep(const DevSim& p, int pair, const Blk bid
     const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
     const long long NP = (long long)p.nx * p.ny;  // sites per plane
     const T* drho = cp<T>(p.rho);
-    const T* j0p = cp<T>(p.j0p);
     const int cur = p.us[pair].cur;
     const U* uold = cp<U>(p.uit[pair][cur]);
     U* unew = mp<U>(p.uit[pair][cur ^ 1]);
@@ -1267,7 +1271,7 @@ __device__ __forceinline__ void b_sweep(const DevSim& p, int pair, const Blk bid
             const long long g = (D == 3 ? zj * NP : 0) + own_xy;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                pj[a] = U(j0p[a * p.N + g]);
+                pj[a] = U(plane<T>(p.j0pp, a)[g]);
                 if (use_d) pd[a] = dvec[a * p.N + g];
             }
         }
@@ -1499,9 +1503,6 @@ __device__ __forceinline__ void b_force(const DevSim& p, int pair, const Blk bid
     const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
     const long long NP = (long long)p.nx * p.ny;
     const T* drho = cp<T>(p.rho);
-    T* j0p = mp<T>(p.j0p);
-    T* fo = mp<T>(p.f);
-    const U* jw = cp<U>(p.jt_warm);
     U* u0 = mp<U>(p.uit[pair][p.us[pair].cur]);
     const int ix = tid % TX, iy = tid / TX;
     const int gx = x0 + ix, gy = y0 + iy;
@@ -1539,8 +1540,8 @@ __device__ __forceinline__ void b_force(const DevSim& p, int pair, const Blk bid
             const long long g = (D == 3 ? z * NP : 0) + own_xy;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
-                pj[a] = j0p[a * p.N + g];
-                pw[a] = p.warm ? jw[a * p.N + g] : U(0);
+                pj[a] = plane<T>(p.j0pp, a)[g];
+                pw[a] = p.warm ? plane<U>(p.jwp, a)[g] : U(0);
             }
         }
     };
@@ -1592,8 +1593,8 @@ __device__ __forceinline__ void b_force(const DevSim& p, int pair, const Blk bid
                 const T lap3 = T(L::T3_AX) * ax + T(L::T3_DIAG) * diag + T(2.0 * L::T3_TWO) * two;
                 const T fa = phys<T>(p).kappa * rs * lap3;
                 const T j = pj[a] + T(0.5) * fa;  // S2: j0' = j0 + (h/2) f
-                fo[a * p.N + g] = fa;
-                j0p[a * p.N + g] = j;
+                plane<T>(p.fpp, a)[g] = fa;
+                plane<T>(p.j0pp, a)[g] = j;
                 u0[a * p.N + g] = (U(j) + pw[a]) / rho;
             }
         }
@@ -1625,7 +1626,6 @@ __device__ __forceinline__ void b_derivs(const DevSim& p, const Blk bid)
     const int z0 = D == 3 ? bid.z * TL::ZB : 0;
     const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
     const T* drho = cp<T>(p.rho);
-    const T* j0p = cp<T>(p.j0p);
     const U* uu = cp<U>(p.uit[0][p.us[0].cur]);  // S8: the converged u
     constexpr int MR = (RX * RY + TL::THREADS - 1) / TL::THREADS;
     int hoff[MR];  // wrapped in-plane offsets of the halo points
@@ -1679,7 +1679,7 @@ __device__ __forceinline__ void b_derivs(const DevSim& p, const Blk bid)
             const int gx = min(x0 + tid % TX, p.nx - 1), gy = min(y0 + tid / TX, p.ny - 1);
             const long long sn = at(p, gx, gy, D == 3 ? zc + kDerivsLead : 0);
 #pragma unroll
-            for (int a = 0; a < D; ++a) prefetch_l2(j0p + a * p.N + sn);
+            for (int a = 0; a < D; ++a) prefetch_l2(plane<T>(p.j0pp, a) + sn);
         }
         if (zc >= z0 && zc < z1) {
             const int gz = D == 3 ? zc : 0;
@@ -1715,7 +1715,7 @@ __device__ __forceinline__ void b_derivs(const DevSim& p, const Blk bid)
                 const T rs = pl[2][3 * PS + ri];
                 T jtl[3] = {T(0), T(0), T(0)};  // j~ = rho u - j0' (S8)
 #pragma unroll
-                for (int a = 0; a < D; ++a) jtl[a] = rs * u[a] - j0p[a * p.N + s];
+                for (int a = 0; a < D; ++a) jtl[a] = rs * u[a] - plane<T>(p.j0pp, a)[s];
                 derivs_tail<LAT, T>(p, s, du, divj, dp, dpr, dpuu, rs, u, jtl);
             }
         }
@@ -1740,7 +1740,6 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
     const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
     const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
     const T* drho = cp<T>(p.rho);
-    const T* j0p = cp<T>(p.j0p);
     const U* uu = cp<U>(p.uit[0][p.us[0].cur]);  // S8: the converged u
     constexpr int MR = (RX * RY + TL::THREADS - 1) / TL::THREADS;
     int hoff[MR];  // wrapped in-plane offsets of the halo points
@@ -1794,7 +1793,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
             const int gx = min(x0 + tid % TX, p.nx - 1), gy = min(y0 + tid / TX, p.ny - 1);
             const long long sn = at(p, gx, gy, D == 3 ? zc + kDerivsLead : 0);
 #pragma unroll
-            for (int a = 0; a < D; ++a) prefetch_l2(j0p + a * p.N + sn);
+            for (int a = 0; a < D; ++a) prefetch_l2(plane<T>(p.j0pp, a) + sn);
         }
         if (zc >= z0 && zc < z1) {
             const int gz = D == 3 ? zc : 0;
@@ -1830,7 +1829,7 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim
                 const T rs = pl[2][3 * PS + ri];
                 T jtl[3] = {T(0), T(0), T(0)};  // j~ = rho u - j0' (S8)
 #pragma unroll
-                for (int a = 0; a < D; ++a) jtl[a] = rs * u[a] - j0p[a * p.N + s];
+                for (int a = 0; a < D; ++a) jtl[a] = rs * u[a] - plane<T>(p.j0pp, a)[s];
                 derivs_tail<LAT, T>(p, s, du, divj, dp, dpr, dpuu, rs, u, jtl);
             }
         }
@@ -1873,12 +1872,8 @@ __device__ __forceinline__ void b_collide(const DevSim& p, int src, const Blk bi
     const int x0 = bid.x * TX, y0 = bid.y * TY;
     const int z0 = D == 3 ? bid.z * TL::ZB : 0;
     const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
-    const T* aux = cp<T>(p.aux);
     const T* drho = cp<T>(p.rho);
-    const T* j0p = cp<T>(p.j0p);
-    const T* fp = cp<T>(p.f);
     const U* uu = cp<U>(p.uit[0][p.us[0].cur]);
-    U* jw = mp<U>(p.jt_warm);
     T k1, k2, k3;
     collision_consts<LAT, T>(p, k1, k2, k3);
     // The halo box starts at x0 - 2, an even column: with nx even, each pair of box columns is
@@ -1903,14 +1898,14 @@ __device__ __forceinline__ void b_collide(const DevSim& p, int src, const Blk bi
                     const long long g = base + goff[m];
 #pragma unroll
                     for (int c = 0; c < NP; ++c)
-                        cp_async<G * sizeof(T)>(dst + c * RY * RX + t * G, aux + (AL::A + c) * p.N + g);
+                        cp_async<G * sizeof(T)>(dst + c * RY * RX + t * G, auxp<T>(p, AL::A + c) + g);
                 }
             }
         } else {
             for (int k = tid; k < RX * RY; k += nth) {
                 const long long g = base + wrapm(x0 - 2 + k % RX, p.nx) + (long long)p.nx * wrapm(y0 - 2 + k / RX, p.ny);
 #pragma unroll
-                for (int c = 0; c < NP; ++c) cp_async<sizeof(T)>(dst + c * RY * RX + k, aux + (AL::A + c) * p.N + g);
+                for (int c = 0; c < NP; ++c) cp_async<sizeof(T)>(dst + c * RY * RX + k, auxp<T>(p, AL::A + c) + g);
             }
         }
     };
@@ -1938,11 +1933,11 @@ __device__ __forceinline__ void b_collide(const DevSim& p, int src, const Blk bi
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 ua[a] = uu[a * p.N + s];
-                j0s[a] = j0p[a * p.N + s];
-                f[a] = fp[a * p.N + s];
+                j0s[a] = plane<T>(p.j0pp, a)[s];
+                f[a] = plane<T>(p.fpp, a)[s];
             }
 #pragma unroll
-            for (int q = 0; q < AL::NB; ++q) sigl[q] = aux[(AL::SIGL + q) * p.N + s];
+            for (int q = 0; q < AL::NB; ++q) sigl[q] = auxp<T>(p, AL::SIGL + q)[s];
         }
         if (PF == 0) {  // 2D: the single plane, in this one pass
             fetch(zl);
@@ -1961,12 +1956,12 @@ __device__ __forceinline__ void b_collide(const DevSim& p, int src, const Blk bi
             const int gx = min(x0 + tid % TX, p.nx - 1), gy = min(y0 + tid / TX, p.ny - 1);
             const long long sn = at(p, gx, gy, D == 3 ? zc + kCollideLead : 0);
 #pragma unroll
-            for (int c = AL::SIGL; c < AL::XI + AL::NX; ++c) prefetch_l2(aux + c * p.N + sn);
+            for (int c = AL::SIGL; c < AL::XI + AL::NX; ++c) prefetch_l2(auxp<T>(p, c) + sn);
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 prefetch_l2(uu + a * p.N + sn);
-                prefetch_l2(j0p + a * p.N + sn);
-                prefetch_l2(fp + a * p.N + sn);
+                prefetch_l2(plane<T>(p.j0pp, a) + sn);
+                prefetch_l2(plane<T>(p.fpp, a) + sn);
             }
             prefetch_l2(drho + sn);
             if (Codec<S>::EXACT) prefetch_l2(cp<float>(p.rho_lo) + sn);
@@ -1986,7 +1981,7 @@ __device__ __forceinline__ void b_collide(const DevSim& p, int src, const Blk bi
                     u[a] = T(ua[a]);
                     const U jta = U(rs) * ua[a] - U(j0s[a]);  // j~ = rho u - j0' (S8)
                     jtl[a] = T(jta);
-                    jw[a * p.N + s] = jta;  // the next step's warm start
+                    plane<U>(p.jwp, a)[s] = jta;  // the next step's warm start
                 }
                 T P, DP, PM, RPP;
                 eos_full<T>(p, rs, P, DP, PM, RPP);
@@ -2021,7 +2016,7 @@ __device__ __forceinline__ void b_collide(const DevSim& p, int src, const Blk bi
                     }
                 T Xi[10];
 #pragma unroll
-                for (int q = 0; q < AL::NX; ++q) Xi[q] = aux[(AL::XI + q) * p.N + s];
+                for (int q = 0; q < AL::NX; ++q) Xi[q] = auxp<T>(p, AL::XI + q)[s];
                 collide_tail<LAT, T, S, READ>(p, src, r, drs, u, f, jtl, Sig, Xi);
             }
         }
