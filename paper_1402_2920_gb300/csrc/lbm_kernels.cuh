@@ -561,7 +561,9 @@ static __device__ double frozen_gain(const DevSim& p, double rho)
 static __device__ void b_us_begin(const DevSim& p, int pair)
 {
     UsolveState& u = p.us[pair];
-    // spectrum bound g of this solve from the density range of the state, with 5 % margin
+    // spectrum bound g of this solve from the density range of the state, with 2 % margin (the
+    // frozen-coefficient value is the largest eigenvalue of a uniform state; a bound the solve
+    // outgrows shows as a growing residual, and the control kernel then falls back to plain sweeps)
     unsigned* rg = p.range + pair * 2 * kRangeSlots;
     float flo = 3.0e38f, fhi = 0.f;
     for (int k = 0; k < kRangeSlots; ++k) {
@@ -574,7 +576,7 @@ static __device__ void b_us_begin(const DevSim& p, int pair)
     if (!(lo > 0.0 && hi >= lo && hi < 1e30)) lo = hi = p.rho0;
     double g = 0.0;
     for (int k = 0; k <= 16; ++k) g = fmax(g, frozen_gain(p, lo + (hi - lo) * k / 16.0));
-    g = fmin(0.95, 1.05 * g);
+    g = fmin(0.95, 1.02 * g);
     u.gain = g;
     u.cheb_delta = 0.5 * g;
     u.cheb_sigma = (1.0 - 0.5 * g) / (0.5 * g);
