@@ -1726,8 +1726,10 @@ __device__ __forceinline__ void b_derivs(const DevSim& p, const Blk bid)
 }
 // The one-simulation kernel keeps its own copy of the body with blockIdx: routing it through
 // b_derivs made it 30 % slower (0.67 against 0.52 ms at 256^3), which the other kernels do not show.
+// With FP32 fields and u-solve three CTAs share an SM (80 registers, 62 KB of shared memory
+// each): 0.474 ms against 0.505 ms for two at 256^3.
 template <int LAT, typename T, typename U>
-__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, 2) k_derivs(DevSim p)
+__global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(T) == 4 && sizeof(U) == 4 ? 3 : 2) k_derivs(DevSim p)
 {
     using L = Lat<LAT>;
     constexpr int D = L::D;

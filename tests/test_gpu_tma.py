@@ -1,8 +1,8 @@
 """The tensor-copy (TMA) form of the u-solve sweep against the per-thread-copy form and the oracle.
 
-LBM_SWEEP_COPY=tma at lbm_create selects the sweep whose interior tiles load their planes of u
-and rho - rho0 with tensor copies tracked by mbarriers (tiles on the periodic seams still copy
-per thread).  Both forms load the same values into the same shared-memory ring, so the results
+The default sweep of a 3D lattice loads the planes of u and rho - rho0 of its interior tiles with
+tensor copies tracked by mbarriers (tiles on the periodic seams still copy per thread);
+LBM_SWEEP_COPY=cp_async at lbm_create selects per-thread copies for every tile.  Both forms load the same values into the same shared-memory ring, so the results
 are bitwise equal; the lattice is large enough in x and y to have interior tiles (x tiles start
 every 32 sites, y tiles every 8, and a box reaches 4 sites beyond its tile).
 """
