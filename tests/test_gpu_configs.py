@@ -118,7 +118,7 @@ def test_config_droplet3d_128_storages_vs_fp64_2000_steps():
     # bounds after 2000 steps, about twice the measured error.  16-bit storages: the global
     # reference rounds the deviation from w_i(rho0) rho0, 10-20 % of n_i across the two phases, to
     # 2^-11 (half) or 2^-8 (bfloat16) each step; the sender's local reference rounds only the
-    # velocity and non-equilibrium parts.  FP32: the benchmark spec's 1e-6 after 1000 steps holds for
+    # velocity and non-equilibrium parts.  FP32: the 1e-6 target after 1000 steps holds for
     # the global-reference deviations; after 2000 steps the slow drift of the droplet's mass
     # balance under FP32 arithmetic has roughly doubled it.
     tols = {"fp32dev": (1e-6, 3e-6), "fp16dev": (None, 3e-3), "bf16dev": (None, 1.5e-2), "fp32loc": (None, 4e-6),

@@ -16,9 +16,9 @@ The Hermite prefactors of Delta^corr (w/(2 c_s^4), w/(6 c_s^6) with the
 c_s^2 traces) and of Delta^int are what these moments fix: a wrong power of
 c_s^2(rho0) or a dropped trace term changes one of them.
 
-Stability: the workloads' T/Tc moved from the survey's 0.96 (2D) and 0.985 (3D)
-to 0.99 and 0.998 because the method's whole update is linearly unstable in
-the gas phase at the deeper quenches.  Uniform gas with 1e-7 noise must grow by
+Stability: the workloads run at T/Tc = 0.99 (2D) and 0.998 (3D), not at the
+deeper 0.96 and 0.985, because the method's whole update is linearly unstable
+in the gas phase at the deeper quenches.  Uniform gas with 1e-7 noise must grow by
 orders of magnitude within a few steps at the deeper T/Tc and decay at the
 workloads' T/Tc.
 """
