@@ -97,8 +97,9 @@ def _algorithmic_bytes(lattice, storage_bytes, read_pops, chebyshev=True):
     return {
         # read the populations, write rho - rho0, rho_lo and j0
         "moments": pops + (2 + d) * f,
-        # read rho - rho0, j0 and the warm-start j~; write f, j0' and the starting u
-        "force": f + 2 * d * f + 3 * d * f,
+        # read rho - rho0, j0 and the last two steps' j~ (the extrapolated start); write f, j0' and
+        # the starting u
+        "force": f + 3 * d * f + 3 * d * f,
         # read u, rho - rho0, j0'; write u (Chebyshev: read and write the update vector too)
         "usolve_sweep": f + 3 * d * f + (2 * d * f if chebyshev else 0),
         # read u, rho - rho0, j0'; write A, B, C, the local Sigma and Xi'
@@ -252,11 +253,12 @@ def run_native(args):
     a, b, T = case.eos_abT
     stream = torch.cuda.current_stream()
 
-    def make_sim(st, usolve=P.LBM_USOLVE_NATIVE):
-        # u-solve sweeps Chebyshev-accelerated for the spectrum bound g over the workload's density range
+    def make_sim(st, usolve=P.LBM_USOLVE_NATIVE, warm=2):
+        # u-solve sweeps Chebyshev-accelerated for the spectrum bound g over the workload's density
+        # range, started from the last two steps' j~ extrapolated
         prm = P.make_params(gamma=case.gamma, kappa=case.kappa, rho0=case.rho0, storage=st,
                             rho_check_min=0.98 * case.eos.rho_g, rho_check_max=1.02 * case.eos.rho_l,
-                            usolve_omega=0.0, usolve_chebyshev=1, usolve_precision=usolve)
+                            usolve_omega=0.0, usolve_chebyshev=1, usolve_precision=usolve, usolve_warm_start=warm)
         return P.Sim(case.lattice, case.dims, P.make_eos(P.LBM_EOS_VDW, a=a, b=b, T=T), prm, stream.cuda_stream)
 
     def timed(sim, K, Wm):
@@ -292,6 +294,7 @@ def run_native(args):
     N = int(np.prod(case.dims))
     sim = make_sim(storage)
     ms, clocks, sweeps, st = timed(sim, K, Wm)
+    tensor_copies = st.usolve_tensor_copies  # 1: the sweeps' plane loads ran as tensor copies (TMA)
     mlups = whole_job_mlups(ws, N, K, ms / 1e3)
     launches = 5 * K + 2 * sweeps  # moments, force, u-solve start, derivs, collide; sweep + control
 
@@ -334,6 +337,13 @@ def run_native(args):
                           "native-precision sweeps"}
             del simx
             torch.cuda.empty_cache()
+        # the u-solve started from the previous step's j~ alone (Sec. IX) instead of the extrapolation
+        simx = make_sim(storage, warm=1)
+        msx, _, sweepsx, _ = timed(simx, K, Wm)
+        extra["warm_start_previous"] = {"value": whole_job_mlups(ws, N, K, msx / 1e3), "unit": UNIT,
+                                        "ms_per_step": msx / K, "usolve_sweeps_per_step": sweepsx / K}
+        del simx
+        torch.cuda.empty_cache()
         # the sweep's per-thread-copy form against its tensor-copy (TMA) form (the default)
         os.environ["LBM_SWEEP_COPY"] = "cp_async"
         try:
@@ -394,12 +404,14 @@ def run_native(args):
                                        "f32loc": "FP32 deviations from the sender's w_i(rho) rho",
                                        "f16loc": "FP16 deviations from the sender's w_i(rho) rho",
                                        "bf16loc": "BF16 deviations from the sender's w_i(rho) rho"}[args.storage],
-                           "usolve": "FP32 sweeps, Chebyshev-accelerated for the spectrum [0, g], stop when "
-                                     "|dj~| of the plain iteration and the applied update are <= 5e-9",
+                           "usolve": "FP32 sweeps, Chebyshev-accelerated for the spectrum [0, g], started from "
+                                     "j~_n + 0.75 (j~_n - j~_n-1), stop when |dj~| of the plain iteration and the "
+                                     "applied update are <= 5e-9",
                            "parallelism": "replicas x%d" % ws, "l2": "inputs (populations %.1f GB) larger than L2" % (2 * 59 * STORAGE_BYTES[args.storage] * N / 2 / 1e9),
                            "sites": N},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "gpu_launches": launches, "usolve_sweeps_per_step": sweeps / K,
+                "usolve_tensor_copies": tensor_copies,
                 "kernel_ms": prof, "serving": serving}
         line.update(extra)
         print(json.dumps(line), flush=True)

@@ -96,7 +96,10 @@ typedef struct {
                               rounding noise the stored populations put into j0 each step   */
     double usolve_rtol;
     int usolve_max_iter;   /* sweep cap per u-solve; <= 0 selects 500                     */
-    int usolve_warm_start; /* 1: start from the previous step's j~ (Sec. IX item 3); 0: from 0 (S1) */
+    int usolve_warm_start; /* 1: start from the previous step's j~ (Sec. IX item 3); 0: from 0 (S1);
+                              2: from j~_n + 0.75 (j~_n - j~_n-1), the last two steps' j~
+                              extrapolated (one more 3-vector field on the device, read once
+                              per step); other values are LBM_E_INVALID_ARG */
     double rho_check_min;  /* create-time EOS check over [rho_check_min, rho_check_max]:  */
     double rho_check_max;  /* c_s^2 window and positive bulk viscosity (App. B); both 0 skip it */
     double usolve_omega;   /* relaxation of each u-solve sweep, j~ += omega (J(j~) - j~), with J
@@ -123,6 +126,10 @@ typedef struct {
     int status;               /* device-recorded error bits: 1 weights window, 2 non-finite
                                  density, 4 u-solve cap, 8 non-finite j~                   */
     int64_t usolve_sweeps_total; /* u-solve sweeps since lbm_init (each is two kernels)   */
+    int usolve_tensor_copies; /* 1 when the most recent u-solve's sweeps loaded the planes of
+                                 interior tiles with tensor copies (TMA), 0 when every tile
+                                 copied per thread (2D, LBM_SWEEP_COPY=cp_async, or rows that
+                                 are not a multiple of 16 bytes)                        */
 } lbm_stats;
 
 /* Create a simulation on the current CUDA device.

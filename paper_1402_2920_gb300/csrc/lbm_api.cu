@@ -185,6 +185,9 @@ void fill_phys(Phys<T>& q, const DevSim& dv, const lbm_eos& e)
     q.cj = T((1.0 - g) * c0);
 }
 
+// warm-start j~ buffers: two for the start extrapolated from the last two steps
+int warm_buffers(const DevSim& dv) { return dv.warm == 2 ? 2 : 1; }
+
 bool is_local(int storage)
 {
     return storage == LBM_STORE_F32_LOC || storage == LBM_STORE_F16_LOC || storage == LBM_STORE_BF16_LOC;
@@ -205,8 +208,8 @@ size_t bytes_per_site(int lattice, int storage, size_t* ssize_out = nullptr)
     // the senders' references of the local-reference storages, one set per population buffer
     const size_t wref = is_local(storage) ? 2 * (lattice == LBM_D3Q59 ? 8 : 6) * 4 : 0;
     // populations (two buffers), rest planes, rho - rho0, j0', f, aux; u iterates (2 x 2),
-    // warm-start j~ and the two Chebyshev update vectors
-    return 2 * Q * ssize + rest + wref + tsize * (1 + 3 + 3 + naux) + usize * (4 * 3 + 3 + 2 * 3);
+    // warm-start j~ (two buffers with the extrapolated start) and the two Chebyshev update vectors
+    return 2 * Q * ssize + rest + wref + tsize * (1 + 3 + 3 + naux) + usize * (4 * 3 + 2 * 3 + 2 * 3);
 }
 
 int validate(int lattice, const int64_t dims[3], int storage)
@@ -438,7 +441,7 @@ int reset_usolve(lbm_sim* s)
     const size_t jbytes = 3 * size_t(s->dev.N) * s->kt.usize;
     for (int pr = 0; pr < 2; ++pr)
         for (int b = 0; b < 2; ++b) LBM_CK(cudaMemsetAsync(s->dev.uit[pr][b], 0, jbytes, s->stream));
-    LBM_CK(cudaMemsetAsync(s->dev.jt_warm, 0, jbytes, s->stream));
+    LBM_CK(cudaMemsetAsync(s->dev.jt_warm, 0, warm_buffers(s->dev) * jbytes, s->stream));
     const int zi = 0;
     LBM_CK(cudaMemcpyAsync(s->dev.status, &zi, sizeof(int), cudaMemcpyHostToDevice, s->stream));
     return LBM_OK;
@@ -644,7 +647,9 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
     if (!(params->usolve_omega >= 0.0 && params->usolve_omega < 2.0)) { lbm_destroy(s); return LBM_E_INVALID_ARG; }
     dv.omega = params->usolve_omega;  // 0: 2/(2 - g) per solve
     dv.maxit = params->usolve_max_iter > 0 ? params->usolve_max_iter : 500;
-    dv.warm = params->usolve_warm_start ? 1 : 0;
+    if (params->usolve_warm_start < 0 || params->usolve_warm_start > 2) { lbm_destroy(s); return LBM_E_INVALID_ARG; }
+    dv.warm = params->usolve_warm_start;
+    dv.wtheta = 0.75;
     {
         double smax = 0.0;  // max_k |(4/3) sin k - (1/6) sin 2k|, the Sec. IV.B symbol
         for (int k = 0; k <= 20000; ++k) {
@@ -674,7 +679,7 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
     rc = rc ? rc : dev_alloc(s, &dv.f, 3 * N * T);
     for (int pr = 0; pr < 2; ++pr)
         for (int b = 0; b < 2; ++b) rc = rc ? rc : dev_alloc(s, &dv.uit[pr][b], 3 * N * U);
-    rc = rc ? rc : dev_alloc(s, &dv.jt_warm, 3 * N * U);
+    rc = rc ? rc : dev_alloc(s, &dv.jt_warm, size_t(warm_buffers(dv)) * 3 * N * U);
     if (s->kt.local_ref) {
         const int nshell = lattice == LBM_D3Q59 ? 8 : 6;
         for (int b = 0; b < 2; ++b) {
@@ -693,7 +698,8 @@ int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm
         for (int a = 0; a < 3; ++a) {
             dv.j0pp[a] = static_cast<char*>(dv.j0p) + size_t(a) * N * T;
             dv.fpp[a] = static_cast<char*>(dv.f) + size_t(a) * N * T;
-            dv.jwp[a] = static_cast<char*>(dv.jt_warm) + size_t(a) * N * U;
+            for (int b = 0; b < 2; ++b)
+                dv.jwp[b][a] = static_cast<char*>(dv.jt_warm) + size_t((warm_buffers(dv) - 1) * b * 3 + a) * N * U;
         }
     }
     void* usp = nullptr;
@@ -963,6 +969,7 @@ int lbm_stats_get(lbm_sim* s, lbm_stats* out)
     out->usolve_resid = u.resid_last;
     out->status = st;
     out->usolve_sweeps_total = u.sweeps_total;
+    out->usolve_tensor_copies = u.tma;
     return LBM_OK;
 }
 
@@ -974,7 +981,7 @@ int lbm_profile(lbm_sim* s, int reps, double* ms_out, int n)
     const int B = s->kt.block, G = nblocks(dv.N, B);
     const int src = s->cur, pair = 1;
     // the collision kernel rewrites the warm-start j~: keep the run's copy aside
-    const size_t jbytes = 3 * size_t(dv.N) * s->kt.usize;
+    const size_t jbytes = size_t(warm_buffers(dv)) * 3 * size_t(dv.N) * s->kt.usize;
     void* keep = nullptr;
     LBM_CK(cudaMallocAsync(&keep, jbytes, s->stream));
     LBM_CK(cudaMemcpyAsync(keep, dv.jt_warm, jbytes, cudaMemcpyDeviceToDevice, s->stream));
@@ -1022,6 +1029,7 @@ namespace {
 struct CkptHeader {
     char magic[8];
     int32_t lattice, storage, usize, Q;
+    int32_t warm_buffers, pad;
     int64_t dims[3];
     int64_t steps;
     double gamma, kappa, rho0;
@@ -1036,7 +1044,7 @@ int lbm_save(lbm_sim* s, const char* path)
     const size_t N = size_t(s->dev.N);
     const size_t pbytes = size_t(s->Q) * N * s->kt.ssize;
     const size_t zbytes = N * s->kt.rsize;
-    const size_t jbytes = 3 * N * s->kt.usize;
+    const size_t jbytes = size_t(warm_buffers(s->dev)) * 3 * N * s->kt.usize;
     const size_t wbytes = s->dev.wref[0] ? size_t(s->d == 3 ? 8 : 6) * N * sizeof(float) : 0;
     std::vector<char> buf(pbytes + zbytes + jbytes + wbytes);
     UsolveState us[2];
@@ -1047,11 +1055,12 @@ int lbm_save(lbm_sim* s, const char* path)
     if (wbytes)  // the senders' references the stored populations are relative to
         LBM_CK(cudaMemcpy(buf.data() + pbytes + zbytes + jbytes, s->dev.wref[s->cur], wbytes, cudaMemcpyDeviceToHost));
     CkptHeader h{};
-    std::memcpy(h.magic, "LBM2PH02", 8);
+    std::memcpy(h.magic, "LBM2PH03", 8);
     h.lattice = s->lattice;
     h.storage = s->prm.storage;
     h.usize = int32_t(s->kt.usize);
     h.Q = s->Q;
+    h.warm_buffers = warm_buffers(s->dev);
     for (int k = 0; k < 3; ++k) h.dims[k] = s->dims[k];
     h.steps = s->steps;
     h.gamma = s->prm.gamma;
@@ -1074,13 +1083,14 @@ int lbm_load(lbm_sim* s, const char* path)
     CkptHeader h{};
     UsolveState u0{};
     bool ok = std::fread(&h, sizeof(h), 1, fp) == 1 && std::fread(&u0, sizeof(u0), 1, fp) == 1;
-    ok = ok && std::memcmp(h.magic, "LBM2PH02", 8) == 0 && h.lattice == s->lattice && h.storage == s->prm.storage &&
+    ok = ok && std::memcmp(h.magic, "LBM2PH03", 8) == 0 && h.lattice == s->lattice && h.storage == s->prm.storage &&
+         h.warm_buffers == warm_buffers(s->dev) &&
          h.usize == int32_t(s->kt.usize) && h.Q == s->Q && h.dims[0] == s->dims[0] && h.dims[1] == s->dims[1] &&
          h.dims[2] == s->dims[2];
     const size_t N = size_t(s->dev.N);
     const size_t pbytes = size_t(s->Q) * N * s->kt.ssize;
     const size_t zbytes = N * s->kt.rsize;
-    const size_t jbytes = 3 * N * s->kt.usize;
+    const size_t jbytes = size_t(warm_buffers(s->dev)) * 3 * N * s->kt.usize;
     const size_t wbytes = s->dev.wref[0] ? size_t(s->d == 3 ? 8 : 6) * N * sizeof(float) : 0;
     std::vector<char> buf;
     if (ok) {

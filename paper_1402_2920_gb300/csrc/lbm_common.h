@@ -34,7 +34,8 @@ struct UsolveState {
     double gain;                    // this solve's bound g, from the density range of the state
     double resid_min;               // smallest residual of the solve so far (divergence guard)
     int mode;                       // 1: Chebyshev acceleration, 0: plain relaxation
-    int pad[2];
+    int wsel;                       // pair 0: the warm-start buffer holding the newest j~ (see jwp)
+    int tma;                        // 1 once a sweep of this solve loaded planes by tensor copies
 };
 
 // planes ahead of the one in work whose per-site inputs the collision and derivative
@@ -84,7 +85,8 @@ struct DevSim {
     void* f;              // T [3][N]: interface force
     void* uit[2][2];      // U [3][N]: u iterates of the u-solve, ping-pong, for pair 0 (the run)
                           // and pair 1 (lbm_fields); u = (j0' + j~)/rho (S3)
-    void* jt_warm;        // U [3][N]: j~ = rho u - j0' of the last step, the warm start (Sec. IX)
+    void* jt_warm;        // U [nw][3][N]: j~ = rho u - j0' of the last step, the warm start (Sec. IX),
+                          // and with the extrapolated start (warm = 2) that of the step before
     void* aux;            // T [26][N]: A, B_ab, C_a, the local part of Sigma_ab, Xi'_abc
     float* wref[2];       // [NSHELL][N] per population buffer (local-reference storages): w_k(c_s^2(rho)) rho
                           // of every site at the collision that sent the populations in that buffer
@@ -107,7 +109,10 @@ struct DevSim {
     int cheb;                        // Chebyshev acceleration of the sweeps
     double s2max;                    // max over k of |s(k)|^2 of the first-derivative symbol (1D)
     void* dvec[2];                   // U [3][N]: previous update of the u-solve, pair 0 and 1
-    int maxit, warm;
+    int maxit;
+    int warm;                        // u-solve start: 0 j~ = 0, 1 the last step's j~, 2 extrapolated
+                                     // from the last two steps' j~ (see jwp)
+    double wtheta;                   // warm = 2: j~ start = j~_n + wtheta (j~_n - j~_n-1)
     Phys<float> pf;                  // the same parameters for FP32 arithmetic
     Phys<double> pd;                 // and for FP64 arithmetic
     // Tensor maps of the sweep's plane loads (TMA) in device memory, valid when tma = 1.
@@ -116,11 +121,14 @@ struct DevSim {
     // plane through this table (one parameter load instead of 64-bit index arithmetic per store)
     void* popp[2][59];
     // plane tables of the aux field (aux + c N) and of the 3-vector fields j0', f and the warm-start
-    // j~ (field + a N), in the field's element type
+    // j~ (field + a N), in the field's element type.  jwp[b]: warm-start buffer b.  The force kernel
+    // starts the u-solve from jwp[wsel] (the newest j~) and, for warm = 2, jwp[wsel ^ 1] (the one
+    // before); the run's k_us_begin flips wsel, and the collision writes the new j~ over the older
+    // one.  With one buffer (warm < 2) both entries name it.
     void* auxp[26];
     void* j0pp[3];
     void* fpp[3];
-    void* jwp[3];
+    void* jwp[2][3];
     int tma;
 };
 

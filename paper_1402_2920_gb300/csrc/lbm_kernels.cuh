@@ -578,6 +578,7 @@ static __device__ void b_us_begin(const DevSim& p, int pair)
     for (int k = 0; k <= 16; ++k) g = fmax(g, frozen_gain(p, lo + (hi - lo) * k / 16.0));
     g = fmin(0.95, 1.02 * g);
     u.gain = g;
+    if (pair == 0) u.wsel ^= 1;  // the run's collision writes this step's j~ over the older one
     u.cheb_delta = 0.5 * g;
     u.cheb_sigma = (1.0 - 0.5 * g) / (0.5 * g);
     u.iter = 0;
@@ -585,6 +586,7 @@ static __device__ void b_us_begin(const DevSim& p, int pair)
     u.jmax_bits = 0ull;
     u.converged = 0;
     u.running = 1;
+    u.tma = 0;
     u.resid_min = 1e300;
     if (p.cheb) {  // first Chebyshev step: x += r / theta
         u.mode = 1;
@@ -1138,7 +1140,9 @@ struct SweepPlan {
     static constexpr size_t OFF_Q = size_t(R) * D * UP * sizeof(U);
     // 128-byte aligned: the rho planes are tensor-copy destinations
     static constexpr size_t OFF_R = (OFF_Q + size_t(NQB) * NQ * QP * sizeof(U) + 127) / 128 * 128;
-    static constexpr size_t BYTES = OFF_R + size_t(R) * UP * sizeof(T);
+    // the dynamic shared memory starts after the static barriers, 16-byte aligned only: the kernel
+    // moves its ring up to the next 128-byte boundary, within this slack
+    static constexpr size_t BYTES = OFF_R + size_t(R) * UP * sizeof(T) + 128;
 };
 
 // S3-S6 fused: one sweep of the u-solve, iterated in u = (j0' + j~)/rho (the same iteration
@@ -1172,9 +1176,12 @@ __device__ __forceinline__ void b_sweep(const DevSim& p, int pair, const Blk bid
     static_assert(TX * TY == NT, "one J site per thread");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long ring_bar[SP::R];  // one per ring slot (TMA)
-    U* su = reinterpret_cast<U*>(smem_raw);             // [R][D][UP]: u
-    U* sq = reinterpret_cast<U*>(smem_raw + SP::OFF_Q);  // [NQB][NQ][QP]: q_ab
-    T* sr = reinterpret_cast<T*>(smem_raw + SP::OFF_R);  // [R][UP]: rho - rho0
+    // tensor copies write 128-byte aligned destinations; the dynamic window itself starts after the
+    // static barriers on a 16-byte boundary
+    unsigned char* sm = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    U* su = reinterpret_cast<U*>(sm);             // [R][D][UP]: u
+    U* sq = reinterpret_cast<U*>(sm + SP::OFF_Q);  // [NQB][NQ][QP]: q_ab
+    T* sr = reinterpret_cast<T*>(sm + SP::OFF_R);  // [R][UP]: rho - rho0
     auto slot = [](int z) { return D == 3 ? (z + 8 * R) % R : 0; };  // z >= -8
     const int tid = threadIdx.x;
     const int x0 = bid.x * TX, y0 = bid.y * TY;
@@ -1241,12 +1248,13 @@ __device__ __forceinline__ void b_sweep(const DevSim& p, int pair, const Blk bid
     bool tma = false;
     if constexpr (D == 3 && TMA) {
         tma = p.tma != 0 && x0 >= 4 && x0 + TX + 4 <= p.nx && y0 >= 4 && y0 + TY + 4 <= p.ny &&
-              (smem_u32(smem_raw) & 127u) == 0;
+              (smem_u32(sm) & 127u) == 0;
         if (tma) {
             if (tid == 0) {
 #pragma unroll
                 for (int k = 0; k < R; ++k) mbar_init(&ring_bar[k], 1);
                 fence_mbar_init();
+                p.us[pair].tma = 1;  // reported by lbm_stats_get
             }
             __syncthreads();
         }
@@ -1305,7 +1313,7 @@ __device__ __forceinline__ void b_sweep(const DevSim& p, int pair, const Blk bid
             cp_async_commit();
         }
         bool late = false;
-        if (tma) {  // plane zl's tensor copies have landed
+        if (tma && zl < z1 + HZ) {  // plane zl's tensor copies have landed (the last phase loads none)
             const int sl = slot(zl);
             late = !mbar_wait(&ring_bar[sl], (phase >> sl) & 1u);
             if (!late) phase ^= 1u << sl;
@@ -1534,16 +1542,22 @@ __device__ __forceinline__ void b_force(const DevSim& p, int pair, const Blk bid
                                                  (long long)p.nx * wrapm(y0 - 2 + k / RX, p.ny));
         }
     };
-    // own-site inputs (j0, warm-start j~), fetched one plane ahead
+    // own-site inputs (j0, warm-start j~), fetched one plane ahead.  The extrapolated start
+    // j~_n + theta (j~_n - j~_n-1) continues the change of the last step.
     T pj[3] = {T(0), T(0), T(0)};
     U pw[3] = {U(0), U(0), U(0)};
+    const int ws = p.us[0].wsel;
+    const U theta = U(p.wtheta);
     auto fetch_own = [&](int z) {
         if (own && z >= z0 && z < z1) {
             const long long g = (D == 3 ? z * NP : 0) + own_xy;
 #pragma unroll
             for (int a = 0; a < D; ++a) {
                 pj[a] = plane<T>(p.j0pp, a)[g];
-                pw[a] = p.warm ? plane<U>(p.jwp, a)[g] : U(0);
+                if (p.warm) {
+                    const U jn = plane<U>(p.jwp[ws], a)[g];
+                    pw[a] = p.warm == 2 ? jn + theta * (jn - plane<U>(p.jwp[ws ^ 1], a)[g]) : jn;
+                }
             }
         }
     };
@@ -1878,6 +1892,7 @@ __device__ __forceinline__ void b_collide(const DevSim& p, int src, const Blk bi
     const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
     const T* drho = cp<T>(p.rho);
     const U* uu = cp<U>(p.uit[0][p.us[0].cur]);
+    const int ws = p.us[0].wsel;  // the warm-start buffer this step's j~ goes to
     T k1, k2, k3;
     collision_consts<LAT, T>(p, k1, k2, k3);
     // The halo box starts at x0 - 2, an even column: with nx even, each pair of box columns is
@@ -1985,7 +2000,7 @@ __device__ __forceinline__ void b_collide(const DevSim& p, int src, const Blk bi
                     u[a] = T(ua[a]);
                     const U jta = U(rs) * ua[a] - U(j0s[a]);  // j~ = rho u - j0' (S8)
                     jtl[a] = T(jta);
-                    plane<U>(p.jwp, a)[s] = jta;  // the next step's warm start
+                    plane<U>(p.jwp[ws], a)[s] = jta;  // the next step's warm start
                 }
                 T P, DP, PM, RPP;
                 eos_full<T>(p, rs, P, DP, PM, RPP);

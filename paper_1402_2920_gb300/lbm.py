@@ -52,7 +52,7 @@ class lbm_stats(ctypes.Structure):
     _fields_ = [("mass", ctypes.c_double), ("mom", ctypes.c_double * 3), ("steps", ctypes.c_int64),
                 ("usolve_iters_last", ctypes.c_int), ("usolve_iters_max", ctypes.c_int),
                 ("usolve_resid", ctypes.c_double), ("status", ctypes.c_int),
-                ("usolve_sweeps_total", ctypes.c_int64)]
+                ("usolve_sweeps_total", ctypes.c_int64), ("usolve_tensor_copies", ctypes.c_int)]
 
 
 class lbm_request(ctypes.Structure):

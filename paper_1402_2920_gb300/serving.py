@@ -16,7 +16,7 @@ def request_dicts(reqs, storage=P.LBM_STORE_F32_DEV, time_scale=1.0, keep_rho=Fa
         a, b, T = case.eos_abT
         prm = P.make_params(gamma=case.gamma, kappa=case.kappa, rho0=case.rho0, storage=storage,
                             rho_check_min=0.98 * case.eos.rho_g, rho_check_max=1.02 * case.eos.rho_l,
-                            usolve_omega=0.0, usolve_chebyshev=1)
+                            usolve_omega=0.0, usolve_chebyshev=1, usolve_warm_start=2)
         d = {"lattice": case.lattice, "dims": case.dims, "eos": P.make_eos(P.LBM_EOS_VDW, a=a, b=b, T=T),
              "params": prm, "steps": r.steps, "arrival_s": r.arrival * time_scale,
              "rho_init": np.ascontiguousarray(case.rho.reshape(-1)), "sites": int(case.rho.size)}

@@ -12,7 +12,8 @@ def test_algorithmic_bytes_per_site():
     # pair, read once by the moments and written once by the collision (2 Q s = 472 B of the
     # metric's definition, plus the rest pair's extra 4 bytes each way)
     b = bench._algorithmic_bytes(1, 4, read_pops=False)
-    assert b == {"moments": 260, "force": 64, "usolve_sweep": 64, "derivs": 132, "collide": 400}
+    # the force kernel reads the last two steps' j~ of the extrapolated u-solve start
+    assert b == {"moments": 260, "force": 76, "usolve_sweep": 64, "derivs": 132, "collide": 400}
     # 16-bit storages halve the population part only
     h = bench._algorithmic_bytes(1, 2, read_pops=False)
     assert b["moments"] - h["moments"] == 58 * 2 and b["collide"] - h["collide"] == 58 * 2

@@ -32,26 +32,33 @@ def test_mass_and_momentum_conserved(storage, tol):
     assert s1.usolve_iters_last >= 1
 
 
-@pytest.mark.parametrize("storage", [P.LBM_STORE_F32, P.LBM_STORE_F16_LOC])
-def test_checkpoint_resume_is_bitwise(tmp_path, storage):
+@pytest.mark.parametrize("storage,warm", [(P.LBM_STORE_F32, 1), (P.LBM_STORE_F16_LOC, 1), (P.LBM_STORE_F32_DEV, 2)])
+def test_checkpoint_resume_is_bitwise(tmp_path, storage, warm):
+    # warm = 2 keeps two steps' j~ (the extrapolated start) and which buffer is the newer one
     case = W.make_case("droplet2d", dims=(48, 40))
-    a = lib_sim(case, storage=storage)
+    a = lib_sim(case, storage=storage, warm=warm, omega=0.0, chebyshev=1)
     a.init(case.rho)
     a.step(7)
     path = os.path.join(tmp_path, "ck.bin")
     a.save(path)
     a.step(9)
-    b = lib_sim(case, storage=storage)
+    b = lib_sim(case, storage=storage, warm=warm, omega=0.0, chebyshev=1)
     b.load(path)
     b.step(9)
     assert np.array_equal(a.populations(), b.populations())
     assert b.stats().steps == 16
+    # a checkpoint of the other warm-start layout is refused
+    c = lib_sim(case, storage=storage, warm=3 - warm, omega=0.0, chebyshev=1)
+    with pytest.raises(P.LbmError) as e:
+        c.load(path)
+    assert e.value.code == P.LBM_E_IO
 
 
-def test_step_split_is_bitwise():
+@pytest.mark.parametrize("warm", [1, 2])
+def test_step_split_is_bitwise(warm):
     case = W.make_case("droplet3d", dims=(16, 18, 20))
-    a = lib_sim(case, storage=P.LBM_STORE_F32)
-    b = lib_sim(case, storage=P.LBM_STORE_F32)
+    a = lib_sim(case, storage=P.LBM_STORE_F32, warm=warm)
+    b = lib_sim(case, storage=P.LBM_STORE_F32, warm=warm)
     a.init(case.rho)
     b.init(case.rho)
     a.step(5)
@@ -97,6 +104,10 @@ def test_invalid_arguments_are_rejected():
     with pytest.raises(P.LbmError) as e:
         P.Sim(P.LBM_D3Q59, (32, 32, 1), eos, P.make_params())
     assert e.value.code == P.LBM_E_INVALID_ARG
+    for warm in (-1, 3):
+        with pytest.raises(P.LbmError) as e:
+            P.Sim(P.LBM_D2Q21, (32, 32), eos, P.make_params(kappa=0.1, usolve_warm_start=warm))
+        assert e.value.code == P.LBM_E_INVALID_ARG
     # the create-time EOS check: a density range where p/rho leaves the window
     with pytest.raises(P.LbmError) as e:
         P.Sim(P.LBM_D2Q21, (32, 32), eos, P.make_params(rho_check_min=0.2, rho_check_max=2.5))
@@ -126,24 +137,27 @@ def test_usolve_cap_is_reported():
 
 @pytest.mark.parametrize("storage", [P.LBM_STORE_F32_DEV, P.LBM_STORE_F16_DEV, P.LBM_STORE_F16_LOC])
 def test_full_size_spinodal_properties(storage):
-    """256^3 D3Q59 spinodal as the benchmark launches it: mass and momentum conservation,
-    a finite state, a converged u-solve, and bitwise covariance under a periodic shift."""
+    """256^3 D3Q59 spinodal as the benchmark launches it (Chebyshev sweeps, extrapolated start,
+    tensor-copy plane loads): mass and momentum conservation, a finite state, a converged u-solve,
+    and bitwise covariance under a periodic shift."""
     import torch
 
     case = W.make_case("spinodal3d")
-    g = lib_sim(case, storage=storage)
+    kw = dict(omega=0.0, chebyshev=1, warm=2)
+    g = lib_sim(case, storage=storage, **kw)
     g.init(case.rho)
     s0 = g.stats()
     g.step(3)
     s1 = g.stats()
     assert s1.status == 0
+    assert s1.usolve_tensor_copies == 1
     assert abs(s1.mass - s0.mass) < 1e-12 * s0.mass
     assert max(abs(v) for v in s1.mom) < 1e-5 * s0.mass
     n = torch.empty((59, case.rho.size), dtype=torch.float64, device="cuda")
     P.lbm_populations(g.handle, n)
     assert bool(torch.isfinite(n).all())
     shift = (5, 11, 3)  # (z, y, x) roll, not a multiple of any block
-    h = lib_sim(case, storage=storage)
+    h = lib_sim(case, storage=storage, **kw)
     h.init(np.ascontiguousarray(np.roll(case.rho, shift, axis=(0, 1, 2))))
     h.step(3)
     m = torch.empty_like(n)

@@ -39,6 +39,9 @@ def test_tma_sweep_is_bitwise_the_per_thread_sweep(storage, kw):
         g.init(case.rho)
         g.step(4)
     assert a.stats().usolve_sweeps_total == b.stats().usolve_sweeps_total
+    # the tensor copies did run (interior tiles exist here), and the other form used none
+    assert a.stats().usolve_tensor_copies == 1
+    assert b.stats().usolve_tensor_copies == 0
     assert np.array_equal(a.populations(), b.populations())
     if storage == P.LBM_STORE_F64:
         o = oracle_sim(case)
