@@ -130,6 +130,7 @@ struct DevSim {
     void* fpp[3];
     void* jwp[2][3];
     int tma;
+    int zb;  // z planes per CTA of the tiled kernels (3D; 1 in 2D), chosen at creation
 };
 
 // The sweep's tensor maps: the u iterates uit[pair][buffer] as {nx, ny, nz, 3} and rho - rho0
@@ -184,7 +185,7 @@ struct KernelTable {
     const void* kb_collide;     // (sims, work)
     const void* kb_step_end;    // (sims, work)
     int block;                // threads per block of the per-site kernels
-    int tile[3];              // TX, TY, ZB of the tiled kernels
+    int tile[2];              // TX, TY of the tiled kernels (the z-slab depth is DevSim::zb)
     int tile_threads;
     size_t smem_force, smem_sweep, smem_derivs, smem_collide;  // dynamic shared memory bytes
     size_t tsize, usize, ssize;  // bytes of T, U and the storage type

@@ -973,15 +973,15 @@ __device__ __forceinline__ void collide_tail(const DevSim& p, int src, const Sit
 }
 
 // ---------------------------------------------------------------------------
-// Tiled kernels.  A CTA owns TX x TY columns of one z-slab and marches along z
-// (2.5D blocking): each plane it loads is kept in a shared-memory ring that
+// Tiled kernels.  A CTA owns TX x TY columns of one z-slab of DevSim::zb planes and marches
+// along z (2.5D blocking): each plane it loads is kept in a shared-memory ring that
 // holds the 5 planes the Sec. IV.B first derivative reaches (2 on each side)
 // plus those in flight, so x and y derivatives read the current plane and z
 // derivatives the ring.  In 2D the ring is the single plane.
 // ---------------------------------------------------------------------------
 template <int D>
 struct Tile {
-    static constexpr int TX = 32, TY = D == 3 ? 8 : 16, ZB = D == 3 ? 32 : 1;
+    static constexpr int TX = 32, TY = D == 3 ? 8 : 16;
     static constexpr int THREADS = TX * TY;
 };
 
@@ -1185,8 +1185,8 @@ __device__ __forceinline__ void b_sweep(const DevSim& p, int pair, const Blk bid
     auto slot = [](int z) { return D == 3 ? (z + 8 * R) % R : 0; };  // z >= -8
     const int tid = threadIdx.x;
     const int x0 = bid.x * TX, y0 = bid.y * TY;
-    const int z0 = D == 3 ? bid.z * TL::ZB : 0;
-    const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
+    const int z0 = D == 3 ? bid.z * p.zb : 0;
+    const int z1 = D == 3 ? min(z0 + p.zb, p.nz) : 1;
     const long long NP = (long long)p.nx * p.ny;  // sites per plane
     const T* drho = cp<T>(p.rho);
     const int cur = p.us[pair].cur;
@@ -1509,8 +1509,8 @@ __device__ __forceinline__ void b_force(const DevSim& p, int pair, const Blk bid
     T* sr = reinterpret_cast<T*>(smem_raw);  // [R][RY][RX]: rho - rho0
     const int tid = threadIdx.x;
     const int x0 = bid.x * TX, y0 = bid.y * TY;
-    const int z0 = D == 3 ? bid.z * TL::ZB : 0;
-    const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
+    const int z0 = D == 3 ? bid.z * p.zb : 0;
+    const int z1 = D == 3 ? min(z0 + p.zb, p.nz) : 1;
     const long long NP = (long long)p.nx * p.ny;
     const T* drho = cp<T>(p.rho);
     U* u0 = mp<U>(p.uit[pair][p.us[pair].cur]);
@@ -1639,8 +1639,8 @@ __device__ __forceinline__ void b_derivs(const DevSim& p, const Blk bid)
     T* sr = reinterpret_cast<T*>(smem_raw);  // [R][NP][RY][RX]
     const int tid = threadIdx.x, nth = blockDim.x;
     const int x0 = bid.x * TX, y0 = bid.y * TY;
-    const int z0 = D == 3 ? bid.z * TL::ZB : 0;
-    const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
+    const int z0 = D == 3 ? bid.z * p.zb : 0;
+    const int z1 = D == 3 ? min(z0 + p.zb, p.nz) : 1;
     const T* drho = cp<T>(p.rho);
     const U* uu = cp<U>(p.uit[0][p.us[0].cur]);  // S8: the converged u
     constexpr int MR = (RX * RY + TL::THREADS - 1) / TL::THREADS;
@@ -1755,8 +1755,8 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS, sizeof(T) == 4 && 
     T* sr = reinterpret_cast<T*>(smem_raw);  // [R][NP][RY][RX]
     const int tid = threadIdx.x, nth = blockDim.x;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
-    const int z0 = D == 3 ? int(blockIdx.z) * TL::ZB : 0;
-    const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
+    const int z0 = D == 3 ? int(blockIdx.z) * p.zb : 0;
+    const int z1 = D == 3 ? min(z0 + p.zb, p.nz) : 1;
     const T* drho = cp<T>(p.rho);
     const U* uu = cp<U>(p.uit[0][p.us[0].cur]);  // S8: the converged u
     constexpr int MR = (RX * RY + TL::THREADS - 1) / TL::THREADS;
@@ -1888,8 +1888,8 @@ __device__ __forceinline__ void b_collide(const DevSim& p, int src, const Blk bi
     T* sr = reinterpret_cast<T*>(smem_raw);  // [R][NP][RY][RX]
     const int tid = threadIdx.x, nth = blockDim.x;
     const int x0 = bid.x * TX, y0 = bid.y * TY;
-    const int z0 = D == 3 ? bid.z * TL::ZB : 0;
-    const int z1 = D == 3 ? min(z0 + TL::ZB, p.nz) : 1;
+    const int z0 = D == 3 ? bid.z * p.zb : 0;
+    const int z1 = D == 3 ? min(z0 + p.zb, p.nz) : 1;
     const T* drho = cp<T>(p.rho);
     const U* uu = cp<U>(p.uit[0][p.us[0].cur]);
     const int ws = p.us[0].wsel;  // the warm-start buffer this step's j~ goes to
@@ -2406,7 +2406,6 @@ KernelTable make_table(bool read_pops)
     using TL = Tile<Lat<LAT>::D>;
     t.tile[0] = TL::TX;
     t.tile[1] = TL::TY;
-    t.tile[2] = TL::ZB;
     t.tile_threads = TL::THREADS;
     constexpr int D = Lat<LAT>::D;
     t.smem_sweep = SweepPlan<D, T, U>::BYTES;

@@ -184,3 +184,26 @@ def test_populations_export_import_roundtrip(storage, tol):
     assert abs(b.stats().mass - a.stats().mass) < 1e-6 * a.stats().mass
     b.step(5)
     assert b.stats().status == 0
+
+
+@pytest.mark.parametrize("zb", [5, 13, 40])
+def test_slab_depth_does_not_change_results(zb):
+    """The tiled kernels' z-slab depth (chosen per lattice at lbm_create; LBM_TILE_Z sets it) only
+    regroups the planes among CTAs: the results are bitwise those of the default depth."""
+    case = W.make_case("droplet3d", dims=(40, 24, 44))
+    kw = dict(storage=P.LBM_STORE_F32_DEV, omega=0.0, chebyshev=1, warm=2)
+    old = os.environ.get("LBM_TILE_Z")
+    os.environ["LBM_TILE_Z"] = str(zb)
+    try:
+        a = lib_sim(case, **kw)
+    finally:
+        if old is None:
+            del os.environ["LBM_TILE_Z"]
+        else:
+            os.environ["LBM_TILE_Z"] = old
+    b = lib_sim(case, **kw)
+    for g in (a, b):
+        g.init(case.rho)
+        g.step(6)
+    assert a.stats().usolve_sweeps_total == b.stats().usolve_sweeps_total
+    assert np.array_equal(a.populations(), b.populations())
