@@ -63,7 +63,8 @@ def _cs0(case):
     return case.eos.T / (1 - case.eos.b * case.rho0) - case.eos.a * case.rho0
 
 
-BENCH = dict(omega=0.0, chebyshev=1)
+# the benchmark's and the serving loop's u-solve: Chebyshev sweeps, extrapolated start
+BENCH = dict(omega=0.0, chebyshev=1, warm=2)
 
 
 @pytest.mark.parametrize("name,steps_oracle,tol_u", [("droplet2d", 3, 5e-4), ("droplet3d", 1, 2e-4)])
