@@ -139,7 +139,11 @@ typedef struct {
  *   cuda_stream: a cudaStream_t (may be NULL for the legacy default stream).
  *   Fails with LBM_E_INVALID_ARG on bad arguments, LBM_E_BULKVISC or LBM_E_WEIGHTS
  *   when the EOS check over [rho_check_min, rho_check_max] fails, LBM_E_OOM when
- *   device memory is short. */
+ *   device memory is short.
+ * Two environment variables, read here, select among launch forms that give bitwise the
+ * same results: LBM_SWEEP_COPY=cp_async makes every tile of the u-solve sweep copy its
+ * planes per thread instead of by tensor copies; LBM_TILE_Z=<n> sets the z-slab depth of
+ * the tiled kernels (otherwise chosen from the lattice and the GPU's SM count). */
 int lbm_create(int lattice, const int64_t dims[3], const lbm_eos* eos, const lbm_params* params,
                void* cuda_stream, lbm_sim** out);
 

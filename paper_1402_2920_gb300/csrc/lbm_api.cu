@@ -403,7 +403,7 @@ bool encode_plane_map(CUtensorMap* m, void* base, int ncomp, size_t esize, const
 // The sweep kernel: the tensor-copy (TMA) form, whose tensor maps need a 3D lattice with rows a
 // multiple of 16 bytes, or per-thread plane copies (2D, other sizes, or LBM_SWEEP_COPY=cp_async in
 // the environment).  The TMA form is the default: at three CTAs per SM it is the faster of the two
-// (0.401 against 0.408 ms at 256^3), the copies no longer issued by every thread.
+// (0.395 against 0.402 ms at 256^3), the copies no longer issued by every thread.
 void setup_sweep_maps(lbm_sim* s)
 {
     DevSim& dv = s->dev;
