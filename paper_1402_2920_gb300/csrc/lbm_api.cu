@@ -265,7 +265,7 @@ int add_step(lbm_sim* s, cudaGraph_t g, cudaGraphNode_t dep, int src, cudaGraphN
     }
     {
         void* a[] = {&dv, &pair};
-        LBM_CK(add_kernel(g, &n3, s->kt.us_begin, dim3(1), 1, a, &n2, 1));
+        LBM_CK(add_kernel(g, &n3, s->kt.us_begin, dim3(1), 32, a, &n2, 1));
     }
     cudaGraphConditionalHandle h;
     LBM_CK(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
@@ -540,7 +540,7 @@ int run_fields(lbm_sim* s)
     const int pair = 1;
     LBM_CK(launch_moments(s, dv, s->cur, pair));
     LBM_CK(launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair));
-    LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
+    LBM_CK(launch(s, s->kt.us_begin, 1, 32, dv, pair));
     cudaGraphConditionalHandle h{};
     const int no = 0;
     for (int it = 0; it < s->dev.maxit + 1; ++it) {
@@ -863,7 +863,7 @@ int step_direct(lbm_sim* s)
     cudaGraphConditionalHandle h{};
     LBM_CK(launch_moments(s, dv, src, pair));
     LBM_CK(launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair));
-    LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
+    LBM_CK(launch(s, s->kt.us_begin, 1, 32, dv, pair));
     for (int it = 0; it < dv.maxit + 1; ++it) {
         LBM_CK(launch_tiled(s, s->sweep, s->kt.smem_sweep, dv, pair));
         LBM_CK(launch(s, s->kt.us_ctl, 1, 1, dv, pair, h, no));
@@ -1054,7 +1054,7 @@ int lbm_profile(lbm_sim* s, int reps, double* ms_out, int n)
     // the scratch u-solve pair; the collision writes the spare population buffer
     LBM_CK(launch_moments(s, dv, src, pair));
     LBM_CK(launch_tiled(s, s->kt.force, s->kt.smem_force, dv, pair));
-    LBM_CK(launch(s, s->kt.us_begin, 1, 1, dv, pair));
+    LBM_CK(launch(s, s->kt.us_begin, 1, 32, dv, pair));
     int rc = LBM_OK;
     for (int k = 0; k < 5 && rc == LBM_OK; ++k) {
         for (int r = 0; r <= reps && rc == LBM_OK; ++r) {
@@ -1267,7 +1267,7 @@ int build_batch_graph(Batch* b)
     }
     {
         void* a[] = {&sims, &w, &pair};
-        LBM_CK(add_kernel(b->g, &n3, kt.kb_us_begin, dim3(1), 32, a, &n2, 1));
+        LBM_CK(add_kernel(b->g, &n3, kt.kb_us_begin, dim3(1), 32 * kBatchSlots, a, &n2, 1));
     }
     cudaGraphConditionalHandle h;
     LBM_CK(cudaGraphConditionalHandleCreate(&h, b->g, 1, cudaGraphCondAssignDefault));

@@ -558,7 +558,9 @@ static __device__ double frozen_gain(const DevSim& p, double rho)
     return p.d * p.s2max / 12.0 * fmax(3.0 * cs2 - DP, cs2);
 }
 
-static __device__ void b_us_begin(const DevSim& p, int pair)
+// One warp (lane 0..31) per solve: the reductions are spread over the lanes (one thread took
+// 22 us per step, most of it in the 17 FP64 gain evaluations one after the other).
+static __device__ void b_us_begin(const DevSim& p, int pair, int lane)
 {
     UsolveState& u = p.us[pair];
     // spectrum bound g of this solve from the density range of the state, with 2 % margin (the
@@ -566,16 +568,23 @@ static __device__ void b_us_begin(const DevSim& p, int pair)
     // outgrows shows as a growing residual, and the control kernel then falls back to plain sweeps)
     unsigned* rg = p.range + pair * 2 * kRangeSlots;
     float flo = 3.0e38f, fhi = 0.f;
-    for (int k = 0; k < kRangeSlots; ++k) {
+    for (int k = lane; k < kRangeSlots; k += 32) {
         flo = fminf(flo, __uint_as_float(rg[k]));
         fhi = fmaxf(fhi, __uint_as_float(rg[kRangeSlots + k]));
         rg[k] = 0x7f7fffffu;  // reset for the next state
         rg[kRangeSlots + k] = 0u;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        flo = fminf(flo, __shfl_xor_sync(0xffffffffu, flo, o));
+        fhi = fmaxf(fhi, __shfl_xor_sync(0xffffffffu, fhi, o));
+    }
     double lo = flo, hi = fhi;
     if (!(lo > 0.0 && hi >= lo && hi < 1e30)) lo = hi = p.rho0;
-    double g = 0.0;
-    for (int k = 0; k <= 16; ++k) g = fmax(g, frozen_gain(p, lo + (hi - lo) * k / 16.0));
+    double g = lane <= 16 ? frozen_gain(p, lo + (hi - lo) * lane / 16.0) : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) g = fmax(g, __shfl_xor_sync(0xffffffffu, g, o));
+    if (lane != 0) return;
     g = fmin(0.95, 1.02 * g);
     u.gain = g;
     if (pair == 0) u.wsel ^= 1;  // the run's collision writes this step's j~ over the older one
@@ -599,7 +608,7 @@ static __device__ void b_us_begin(const DevSim& p, int pair)
         u.c2 = p.omega > 0.0 ? p.omega : 2.0 / (2.0 - g);
     }
 }
-static __global__ void k_us_begin(DevSim p, int pair) { b_us_begin(p, pair); }
+static __global__ void k_us_begin(DevSim p, int pair) { b_us_begin(p, pair, threadIdx.x & 31); }  // one warp
 
 // One thread: the S6 test, the S7 swap, and the loop condition of the graph.
 // Returns whether the solve stopped.
@@ -2123,8 +2132,8 @@ __global__ void __launch_bounds__(Tile<Lat<LAT>::D>::THREADS) kb_force(const Dev
 
 static __global__ void kb_us_begin(const DevSim* sims, const BatchWork* w, int pair)
 {
-    const int k = threadIdx.x;
-    if (k < w->nslot && w->live[k]) b_us_begin(sims[k], pair);
+    const int k = threadIdx.x >> 5;  // one warp per slot (the condition is uniform in the warp)
+    if (k < w->nslot && w->live[k]) b_us_begin(sims[k], pair, threadIdx.x & 31);
 }
 
 template <int LAT, typename T, typename U>
