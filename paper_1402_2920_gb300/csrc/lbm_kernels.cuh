@@ -2215,7 +2215,11 @@ __global__ void k_init_eq(DevSim p, const double* rho_in, const double* u_in, in
     T uu = T(0);
 #pragma unroll
     for (int a = 0; a < L::D; ++a) uu += u[a] * u[a];
-    double stored_sum = 0.0;  // initialisation is not on the hot path: FP64 is fine here
+    // sum of the stored values: a float pair (error-free TwoSum, as in the collision) for the
+    // 32-bit arithmetic, whose FP64 adds took most of the kernel's time on GB300; FP64 for the FP64
+    // storage and the local-reference storages
+    double stored_sum = 0.0;
+    float sh = 0.f, sl = 0.f;
     const float* wf = C::LOC ? p.wref[dst] : nullptr;
     const int x = int(s % p.nx), y = int((s / p.nx) % p.ny), z = int(s / ((long long)p.nx * p.ny));
 #pragma unroll
@@ -2236,8 +2240,11 @@ __global__ void k_init_eq(DevSim p, const double* rho_in, const double* u_in, in
         const T dev = w * rs * X + w * drs +
                       phys<T>(p).rho0 * dcs2 *
                           (T(L::wc(k, 1)) + T(L::wc(k, 2)) * (cs2 + cs0) + T(L::wc(k, 3)) * (cs2 * cs2 + cs2 * cs0 + cs0 * cs0));
-        stored_sum += double(pop_put<LAT, S, T>(p, dst, i, s, C::DEV ? dev : w * rs * (T(1) + X)));
+        const T sv = pop_put<LAT, S, T>(p, dst, i, s, C::DEV ? dev : w * rs * (T(1) + X));
+        if constexpr (sizeof(T) == 4) acc2(sh, sl, float(sv));
+        else stored_sum += double(sv);
     }
+    if (sizeof(T) == 4 && !C::LOC) stored_sum = double(sh) + double(sl);
     // the rest population closes the sum to rho (as the collision does)
     if (C::LOC) stored_sum += double(wf[s]);  // the rest population's own reference
     const double rest = (C::DEV && !C::LOC ? rho_in[s] - p.rho0 : rho_in[s]) - stored_sum;
