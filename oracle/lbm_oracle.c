@@ -33,8 +33,11 @@
  * 3D->2D projection; equilibrium: its closed-form moments; stencils: Table
  * III moment conditions and exactness on polynomials; collision: the moment
  * identities of Secs. V, VI, VIII; the step: conservation, steady states,
- * the u-solve fixed point, and the viscosities of Sec. VII).  The Sigma and
- * Xi' algebra of S11 beyond what those identities fix is "parity unpinned".
+ * the u-solve fixed point, the viscosities of Sec. VII, the linear
+ * instability of the gas phase below the workloads' temperatures, and flat
+ * slabs relaxing to the Maxwell coexistence densities of the van der Waals
+ * and of App. B's psi-sine equations of state).  The Sigma and Xi' algebra of
+ * S11 beyond what those identities fix is "parity unpinned".
  */
 #include <math.h>
 #include <stdint.h>
